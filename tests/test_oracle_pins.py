@@ -1,0 +1,548 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: brute-force geometry, closed-form
+eigenpairs, exactness on linear fields, conservation identities, printed constants, or the observed
+convergence order against the analytic Taylor-Green vortex.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+PER = (0, 0, 0, 0, 0, 0)
+SLIPBOX = (3, 3, 3, 3, 3, 3)
+
+
+def centres(n):
+    return np.arange(n) + 0.5
+
+
+# --------------------------------------------------------------------------------------------------
+# Classification (Sec. 2.4.1)
+
+def _links_expected_box(nx, ny, nz, lo, hi):
+    """Brute force for an axis-aligned box: a link is cut iff exactly one of its two centres lies
+    inside; t is the crossing's position on the centre-to-centre segment."""
+    exp = {}
+    N = nx * ny * nz
+    dims = (nx, ny, nz)
+    for a in range(3):
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    x = [i, j, k]
+                    if x[a] + 1 >= dims[a]:
+                        continue
+                    y = list(x)
+                    y[a] += 1
+                    cP = np.array(x) + 0.5
+                    cN = np.array(y) + 0.5
+                    inP = np.all((cP > lo) & (cP < hi))
+                    inN = np.all((cN > lo) & (cN < hi))
+                    b, c = (a + 1) % 3, (a + 2) % 3
+                    inside_trans = lo[b] < cP[b] < hi[b] and lo[c] < cP[c] < hi[c]
+                    ts = []
+                    if inside_trans:
+                        for plane in (lo[a], hi[a]):
+                            t = plane - cP[a]
+                            if 0.0 <= t < 1.0:
+                                ts.append(t)
+                    assert (inP != inN) == (len(ts) % 2 == 1)
+                    if ts:
+                        exp[a * N + (i + nx * (j + ny * k))] = (min(ts), max(ts))
+    return exp
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_classify_box_matches_brute_force(m):
+    nx, ny, nz = 12, 10, 9
+    lo = np.array([2.3, 1.7, 2.9], np.float32).astype(np.float64)
+    hi = np.array([8.6, 7.2, 6.05], np.float32).astype(np.float64)
+    tri = W.axis_box(lo, hi, m)
+    case = oracle.Case(nx, ny, nz)
+    fid, tlo, thi = case.classify(tri)
+    exp = _links_expected_box(nx, ny, nz, lo, hi)
+    assert sorted(exp) == list(fid)
+    for f, a, b in zip(fid, tlo, thi):
+        assert abs(a - exp[f][0]) < 1e-12 and abs(b - exp[f][1]) < 1e-12
+    # flag bits are the two ends of every cut face
+    N = nx * ny * nz
+    fl = np.zeros(N, np.uint8)
+    for f in fid:
+        a, c = divmod(int(f), N)
+        st = (1, nx, nx * ny)[a]
+        fl[c] |= 1 << (2 * a + 1)
+        fl[c + st] |= 1 << (2 * a)
+    assert np.array_equal(fl, case.flags)
+
+
+def test_classify_convex_icosphere_halfspace():
+    """Convex closed soup: cut(link) <=> inside(P) != inside(N) by half-space tests, and t_lo/t_hi are
+    the entry/exit parameters of the segment through the polytope."""
+    n = 16
+    tri = W.icosphere(2, 5.3, (8.3, 7.9, 8.1)).astype(np.float64)
+    A, B, Cv = tri[:, 0], tri[:, 1], tri[:, 2]
+    nrm = np.cross(B - A, Cv - A)
+    outward = np.einsum("ij,ij->i", nrm, A - np.array([8.3, 7.9, 8.1])) > 0
+    nrm[~outward] *= -1
+    off = np.einsum("ij,ij->i", nrm, A)
+    case = oracle.Case(n, n, n)
+    fid, tlo, thi = case.classify(tri.astype(np.float32))
+    got = {int(f): (a, b) for f, a, b in zip(fid, tlo, thi)}
+    N = n ** 3
+    checked = 0
+    for a in range(3):
+        for i in range(n):
+            for j in range(n):
+                for k in range(n):
+                    x = [i, j, k]
+                    if x[a] == n - 1:
+                        continue
+                    P = np.array(x) + 0.5
+                    fidx = a * N + (i + n * (j + n * k))
+                    dn = nrm[:, a]
+                    v0 = P @ nrm.T - off              # < 0 on the inner side of every face plane
+                    if np.any(np.abs(v0) < 1e-7) or np.any(np.abs(v0 + dn) < 1e-7):
+                        continue                      # a centre on a face plane: ambiguous, skip
+                    checked += 1
+                    # slab method: the segment P + t e_a, t in [0, 1), is inside where all v < 0
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        tc = -v0 / dn
+                    par = dn == 0
+                    if np.any(par & (v0 >= 0)):
+                        t_in, t_out = np.inf, -np.inf  # parallel to and outside some face
+                    else:
+                        t_in = np.max(np.where(dn < 0, tc, -np.inf))
+                        t_out = np.min(np.where(dn > 0, tc, np.inf))
+                    ts = [t for t in (t_in, t_out) if t_in < t_out and 0.0 <= t < 1.0]
+                    assert (fidx in got) == bool(ts), (a, x, ts)
+                    p_in = bool(np.all(v0 < 0))
+                    n_in = bool(np.all(v0 + dn < 0))
+                    if len(ts) == 1:
+                        assert p_in != n_in
+                    if ts:
+                        assert abs(got[fidx][0] - min(ts)) < 1e-9
+                        assert abs(got[fidx][1] - max(ts)) < 1e-9
+    assert checked > 3 * 14 * 16 * 16 * 0.9
+
+
+def test_classify_matches_moller_trumbore_on_random_soup():
+    tri = W.random_soup(3000, (0, 0, 0), (20, 16, 12), 4.0, seed=11)
+    case = oracle.Case(20, 16, 12)
+    assert case.mt_disagreements(tri) == 0
+
+
+def test_classify_skips_nonfinite_and_outside():
+    tri = W.random_soup(50, (0, 0, 0), (8, 8, 8), 3.0, seed=5)
+    bad = tri.copy()
+    bad[3, 1, 2] = np.nan
+    bad[7, 0, 0] = np.inf
+    far = (tri + 1000.0).astype(np.float32)
+    case = oracle.Case(8, 8, 8)
+    case.classify(np.concatenate([bad, far]))
+    assert case.n_skipped == 2
+    ref = oracle.Case(8, 8, 8)
+    keep = np.ones(50, bool); keep[[3, 7]] = False
+    ref.classify(tri[keep])
+    assert np.array_equal(case.cut[0], ref.cut[0]) and np.array_equal(case.flags, ref.flags)
+
+
+def test_coplanar_triangle_gives_no_hit():
+    # triangle in the plane y = 2.5 contains grid lines along x and z: W = 0 for them
+    tri = np.array([[[0.2, 2.5, 0.3], [7.1, 2.5, 0.4], [0.5, 2.5, 6.6]]], np.float32)
+    case = oracle.Case(8, 8, 8)
+    fid, _, _ = case.classify(tri)
+    assert all(int(f) // 512 == 1 for f in fid)   # only y-links can be cut
+
+
+# --------------------------------------------------------------------------------------------------
+# Ghost values (Eq. q_axis), distribution function (Eq. distribution_function)
+
+def _wall_case(x0, n=12, extra=None):
+    """A full plane wall x = x0 across a slip box, optionally a second wall."""
+    walls = [x0] + ([] if extra is None else [extra])
+    tri = []
+    for xw in walls:
+        tri.append([[xw, -1.0, -1.0], [xw, 3 * n, -1.0], [xw, -1.0, 3 * n]])
+    case = oracle.Case(n, 6, 5, bc=SLIPBOX)
+    case.set_geometry(np.array(tri, np.float32))
+    return case
+
+
+@pytest.mark.parametrize("x0", [5.03, 5.2, 5.49, 5.5, 5.51, 5.77, 5.97])
+def test_ghost_exact_for_linear_field(x0):
+    """For q = beta (x - x0) the wall value is 0 and the ghost must equal the linear extrapolant q(x_N)
+    on both sides of the wall (upper and lower branch)."""
+    x0 = float(np.float32(x0))
+    case = _wall_case(x0)
+    nx, ny, nz = 12, 6, 5
+    xc = np.arange(nx) + 0.5
+    q = np.broadcast_to(0.7 * (xc - x0), (nz, ny, nx))
+    u = np.stack([q, 2 * q, -q]).reshape(-1)
+    f = int(np.floor(x0 - 0.5))
+    for comp, scale in ((0, 0.7), (1, 1.4), (2, -0.7)):
+        for (i, side) in ((f, +1), (f + 1, -1)):
+            P = i + nx * (2 + ny * 3)
+            g = case.velocity_across(u, comp, P, 0, side)
+            assert g == pytest.approx(scale * (xc[i] + side - x0), abs=1e-12)
+    br = set(case.rec["branch"].tolist())
+    assert br <= {0, 1}
+
+
+def test_ghost_branch_c_when_opposite_is_blocked():
+    # cell 4 (centre 4.5): +x wall at 4.9 (d = 0.4 < 0.5) and a -x wall at 4.2, so the opposite
+    # neighbour O = cell 3 is behind a wall and the lower branch cannot be used -> branch C
+    case = _wall_case(float(np.float32(4.9)), extra=float(np.float32(4.2)))
+    r = case.rec
+    sel = (r["cell"] % 12 == 4) & (r["side"] == 1)
+    assert sel.sum() == 30 and np.all(r["branch"][sel] == 2) and np.all(r["opp"][sel] == -1)
+    # branch C is the upper branch evaluated at d = 1/2: ghost = 2 q_IB - q_P
+    assert np.all(r["c_ib"][sel] == 2.0) and np.all(r["c_p"][sel] == -1.0)
+    assert np.all(r["c_o"][sel] == 0.0)
+
+
+def test_distribution_weights_match_printed_values():
+    gold = GOLD["distribution_function_samples"]
+    for d, wf, wg in zip(gold["d"][1:], gold["fluid_side"][1:], gold["ghost_side"][1:]):
+        case = _wall_case(float(np.float32(5.5 + d)))
+        r = case.rec
+        sel = (r["side"] == 1)
+        assert np.allclose(r["d"][sel], d, atol=1e-6)
+        assert np.allclose(r["w_near"][sel], wf, atol=1e-6)
+        assert np.allclose(r["w_far"][sel], wg, atol=1e-6)
+        assert np.allclose(r["w_near"] + r["w_far"], 1.0 / (1.0 + r["d"]), rtol=1e-14)
+
+
+def test_setup_regions_and_deadend_bits():
+    case = oracle.Case(10, 10, 10)
+    case.set_geometry(W.axis_box((3.2, 3.3, 3.4), (6.6, 6.7, 6.8), 1))
+    fl = case.flags
+    inc = (fl & 63) != 0
+    assert np.array_equal(inc, (fl & 64) != 0)
+    adj = (fl & 128) != 0
+    assert not np.any(adj & inc)
+    # every Omega_adj cell touches an Omega_inc cell and vice versa every neighbour of inc is inc|adj
+    F = fl.reshape(10, 10, 10)
+    I = (F & 64) != 0
+    A = (F & 128) != 0
+    nb = np.zeros_like(I)
+    for ax in range(3):
+        for s in (-1, 1):
+            sh = np.roll(I, s, axis=ax)
+            edge = [slice(None)] * 3
+            edge[ax] = 0 if s == 1 else -1
+            sh[tuple(edge)] = False
+            nb |= sh
+    assert np.array_equal(A, nb & ~I)
+    assert len(case.rec) == 2 * len(case.cut[0])
+
+
+# --------------------------------------------------------------------------------------------------
+# CSM (Sec. 2.3)
+
+def _interior(nx, ny, nz):
+    m = np.zeros((nz, ny, nx), bool)
+    m[1:-1, 1:-1, 1:-1] = True
+    return m.reshape(-1)
+
+
+def _linear_field(n, G):
+    """u_b = sum_a G[a][b] x_a sampled at cell centres (G[a][b] = du_b/dx_a)."""
+    x = centres(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    pos = [X, Y, Z]
+    return np.stack([sum(G[a][b] * pos[a] for a in range(3)) for b in range(3)]).reshape(-1)
+
+
+def test_csm_closed_forms():
+    n = 7
+    case = oracle.Case(n, n, n, bc=SLIPBOX)
+    m = _interior(n, n, n)
+    rot = [[0, 1, 0], [-1, 0, 0], [0, 0, 0]]          # u = (-y, x, 0): rigid rotation
+    assert np.all(case.csm(_linear_field(n, rot))[m] == 0.0)
+    strain = [[1, 0, 0], [0, -1, 0], [0, 0, 0]]       # u = (x, -y, 0): F_CS = -1, C = C1
+    nut = case.csm(_linear_field(n, strain))[m]
+    assert np.allclose(nut, GOLD["csm_C1"]["value"] * np.sqrt(2.0), rtol=1e-14)
+    shear = [[0, 0, 0], [1, 0, 0], [0, 0, 0]]         # u = (y, 0, 0): Q = 0
+    assert np.allclose(case.csm(_linear_field(n, shear))[m], 0.0, atol=1e-16)
+    # |F_CS| <= 1 bounds nu_t <= C1 dx^2 |S|
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(3 * n ** 3)
+    nut = case.csm(u)
+    assert np.all(nut >= 0.0)
+    case2 = oracle.Case(n, n, n, dx=0.5, bc=SLIPBOX)
+    nut2 = case2.csm(u)
+    assert np.allclose(nut2, nut * 0.25 / 0.5, rtol=1e-12)   # nu_t ~ dx^2 * |S| ~ dx^2 / dx
+
+
+def test_csm_random_gradient_bound():
+    n = 5
+    case = oracle.Case(n, n, n, bc=SLIPBOX)
+    m = _interior(n, n, n)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        G = rng.standard_normal((3, 3))
+        nut = case.csm(_linear_field(n, G))[m]
+        S = 0.5 * (G + G.T)
+        Wt = 0.5 * (G - G.T)
+        SS, WW = np.sum(S * S), np.sum(Wt * Wt)
+        F = (WW - SS) / (WW + SS)
+        assert abs(F) <= 1.0
+        assert np.allclose(nut, 0.05 * abs(F) ** 1.5 * np.sqrt(SS), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------------------------------
+# Predictor (Sec. 2.1): conservation and consistency
+
+def test_predictor_conserves_momentum_periodic():
+    n = 8
+    rng = np.random.default_rng(1)
+    case = oracle.Case(n, n, n, nu=0.05, dt=0.1, bc=PER)
+    u = rng.standard_normal(3 * n ** 3)
+    U = case.faces(u)
+    nut = case.csm(u)
+    H, _ = case.predict(u, U, nut, np.zeros_like(u), True)
+    Hs = H.reshape(3, -1).sum(1)
+    assert np.all(np.abs(Hs) < 1e-11 * np.abs(H).sum())
+
+
+def test_predictor_uniform_flow_is_steady():
+    n = 6
+    case = oracle.Case(n, n, n, nu=0.05, dt=0.1, bc=PER)
+    u = np.concatenate([np.full(n ** 3, 0.3), np.full(n ** 3, -0.2), np.full(n ** 3, 0.1)])
+    H, us = case.predict(u, case.faces(u), case.csm(u), np.zeros_like(u), True)
+    assert np.all(H == 0.0) and np.array_equal(us, u)
+
+
+def test_predictor_diffusion_of_a_sine_mode():
+    """Pure diffusion (U = 0, nu_t = 0) of u_x = sin(2 pi y / n) in a periodic box: the discrete
+    Laplacian eigenvalue -(2 - 2 cos(2 pi / n)) nu / dx^2 is exact."""
+    n = 16
+    case = oracle.Case(n, n, 4, nu=0.3, dt=0.1, bc=PER, csm_on=0)
+    y = centres(n)
+    ux = np.broadcast_to(np.sin(2 * np.pi * y / n)[None, :, None], (4, n, n))
+    u = np.stack([ux, 0 * ux, 0 * ux]).reshape(-1)
+    H, _ = case.predict(u, np.zeros(case.NF), np.zeros(case.N), np.zeros_like(u), True)
+    lam = -(2 - 2 * np.cos(2 * np.pi / n)) * 0.3
+    assert np.allclose(H[:case.N], lam * u[:case.N], atol=1e-14)
+    assert np.all(H[case.N:] == 0)
+
+
+# --------------------------------------------------------------------------------------------------
+# Poisson operator and solvers (Eq. poisson)
+
+def _mode(n, kind, k):
+    i = centres(n) - 0.5 + 0.5  # (i + 1/2)
+    if kind == "per":
+        th = 2 * np.pi * k / n
+        return np.cos(th * i), -(2 - 2 * np.cos(th))
+    if kind == "neu":
+        th = np.pi * k / n
+        return np.cos(th * i), -(2 - 2 * np.cos(th))
+    th = np.pi * (k + 0.5) / n      # Neumann at the low face, p = 0 at the high face
+    return np.cos(th * i), -(2 - 2 * np.cos(th))
+
+
+@pytest.mark.parametrize("bcx,kind", [(0, "per"), (3, "neu"), (2, "dir")])
+def test_poisson_operator_eigenpairs(bcx, kind):
+    nx, ny, nz = 12, 8, 6
+    dx = 0.7
+    bc = [bcx, bcx, 3, 3, 0, 0]
+    if kind == "dir":
+        bc[0] = 1
+    case = oracle.Case(nx, ny, nz, dx=dx, bc=tuple(bc))
+    mx, lx = _mode(nx, kind, 3)
+    my, ly = _mode(ny, "neu", 2)
+    mz, lz = _mode(nz, "per", 1)
+    p = (mz[:, None, None] * my[None, :, None] * mx[None, None, :]).reshape(-1)
+    Ap = case.apply(p)
+    lam = (lx + ly + lz) / dx ** 2
+    assert np.allclose(Ap, lam * p, atol=1e-12 * np.abs(lam))
+
+
+def test_poisson_operator_decouples_at_a_cut_wall():
+    nx = 10
+    case = _wall_case(float(np.float32(4.3)), n=nx)   # cuts the x-link between cells 3 and 4
+    # on cells 0..3 the wall is a Neumann face: cos modes of the 4-cell block are eigenvectors
+    th = np.pi * 1 / 4
+    blk = np.cos(th * (centres(4)))
+    p = np.zeros((5, 6, nx))
+    p[:, :, :4] = blk
+    Ap = case.apply(p.reshape(-1)).reshape(5, 6, nx)
+    lam = -(2 - 2 * np.cos(th))
+    assert np.allclose(Ap[:, :, :4], lam * p[:, :, :4], atol=1e-13)
+    assert np.allclose(Ap[:, :, 4:], 0.0)
+
+
+@pytest.mark.parametrize("solver", [oracle.BICGSTAB, oracle.CG, oracle.RBSOR])
+def test_poisson_solve_recovers_eigenmode(solver):
+    nx, ny, nz = 16, 8, 8
+    case = oracle.Case(nx, ny, nz, bc=(1, 2, 3, 3, 3, 3))
+    mx, lx = _mode(nx, "dir", 1)
+    my, ly = _mode(ny, "neu", 1)
+    phi = (np.ones(nz)[:, None, None] * my[None, :, None] * mx[None, None, :]).reshape(-1)
+    lam = lx + ly
+    omega = 1.0 if solver != oracle.RBSOR else 1.7
+    p, st = case.solve(phi, tol=1e-11, solver=solver, omega=omega, maxit=20000)
+    assert st.status == 0 and st.relres <= 1e-11
+    assert np.allclose(p, phi / lam, atol=1e-9 * np.abs(phi / lam).max())
+
+
+# --------------------------------------------------------------------------------------------------
+# Whole step: projection identity, mass balance, momentum, Taylor-Green convergence
+
+def _pieces(case, state, tol=1e-12):
+    u, U = state["u"], state["U"]
+    nut = case.csm(u)
+    H, us = case.predict(u, U, nut, state["H"], state["n"] == 0)
+    us2, _ = case.forcing(us)
+    Us = case.faces(us2)
+    b = case.rhs(Us)
+    p, st = case.solve(b, state["p"], tol=tol)
+    un, Un = case.correct(us2, Us, p)
+    return dict(us=us2, Us=Us, b=b, p=p, u=un, U=Un, st=st)
+
+
+def _div_faces(U, nx, ny, nz, dx):
+    Ux, Uy, Uz = oracle.split_faces(U, nx, ny, nz)
+    return (np.diff(Ux, axis=2) + np.diff(Uy, axis=1) + np.diff(Uz, axis=0)).reshape(-1) / dx
+
+
+def test_projection_identity_and_mass_balance():
+    cfg = W.get_config("sphere_64x32x32")
+    case = oracle.Case(32, 16, 16, 1.0, cfg.nu, cfg.dt, cfg.bc)
+    case.set_geometry(W.icosphere(2, 3.1, (10.2, 8.1, 7.9)))
+    state = case.initial_state(W.initial_fields(W.Config("t", 32, 16, 16, 0, 0, 0, 0, 0, cfg.bc,
+                                                         seed=7)))
+    r = _pieces(case, state, tol=1e-6)
+    div = _div_faces(r["U"], 32, 16, 16, 1.0)
+    res = r["b"] - case.apply(r["p"])
+    assert np.allclose(div, cfg.dt * res, atol=1e-12 * np.abs(r["b"]).max() * cfg.dt)
+    Ux, Uy, Uz = oracle.split_faces(r["Us"], 32, 16, 16)
+    assert abs(Ux[:, :, 0].sum() - Ux[:, :, -1].sum()) < 1e-12 * Ux[:, :, 0].size
+    assert np.all(Uy[:, 0] == 0) and np.all(Uy[:, -1] == 0)
+    # cut faces carry no flux
+    fid = case.cut[0]
+    N = case.N
+    for f in fid[:50]:
+        a, c = divmod(int(f), N)
+        k, rem = divmod(c, 32 * 16)
+        j, i = divmod(rem, 32)
+        face = (Ux[k, j, i + 1], Uy[k, j + 1, i], Uz[k + 1, j, i])[a]
+        assert face == 0.0
+
+
+def test_step_conserves_momentum_periodic():
+    n = 12
+    u0, _, dx = W.taylor_green(n, 0.0, 100.0, nz=2)
+    rng = np.random.default_rng(2)
+    u0 = u0 + 0.05 * rng.standard_normal(u0.shape)
+    case = oracle.Case(n, n, 2, dx, 0.01, 0.01, PER)
+    st = case.initial_state(u0)
+    m0 = st["u"].reshape(3, -1).sum(1)
+    for _ in range(3):
+        case.step(st, tol=1e-12)
+    m1 = st["u"].reshape(3, -1).sum(1)
+    assert np.allclose(m0, m1, atol=1e-10)
+
+
+@pytest.mark.slow
+def test_taylor_green_second_order_without_ib():
+    """Sec. 2.5: without the IB the scheme is second order in space (error ratio ~4 per halving)."""
+    re, dt, nsteps = 100.0, 2e-3, 50
+    errs = []
+    for n in (16, 32, 64):
+        u0, _, dx = W.taylor_green(n, 0.0, re)
+        case = oracle.Case(n, n, 1, dx, 1.0 / re, dt, PER, csm_on=0, forcing_on=0)
+        st = case.initial_state(u0)
+        for _ in range(nsteps):
+            case.step(st, tol=1e-12)
+        ua, _, _ = W.taylor_green(n, nsteps * dt, re)
+        e = st["u"].reshape(3, -1)[0] - ua[0].reshape(-1)
+        errs.append(np.sqrt(np.mean(e ** 2)))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((slopes > 1.8) & (slopes < 2.3)), (errs, slopes)
+    # the decay rate of the velocity amplitude matches exp(-2 pi^2 t / Re)
+    assert GOLD["taylor_green"]["velocity_decay_rate"] == pytest.approx(2 * np.pi ** 2 / re)
+
+
+# --------------------------------------------------------------------------------------------------
+# Forcing (Eq. forcing_term, discrete_forcing_term, distribution_function) and dead-end filter
+
+def test_forcing_zero_at_wall_velocity_and_linear():
+    case = _wall_case(float(np.float32(5.3)))
+    N = case.N
+    us = np.zeros(3 * N)
+    out, fs = case.forcing(us)
+    assert np.all(out == 0.0) and np.all(fs == 0.0)
+    rng = np.random.default_rng(4)
+    us = rng.standard_normal(3 * N)
+    o1, f1 = case.forcing(us)
+    o2, f2 = case.forcing(2.5 * us)
+    assert np.allclose(o2 - 2.5 * us, 2.5 * (o1 - us), atol=1e-12)
+    # one record pair: cell P (centre 4.5) sees the wall at d = 0.8, its far cell G = 5 at 0.2
+    u = np.zeros(3 * N)
+    u[:N] = 1.0
+    o, _ = case.forcing(u)
+    x = np.arange(N) % 12
+    d = float(np.float32(5.3)) - 4.5
+    wn, wf = d / (1 + d), (1 - d) / (1 + d)
+    # P gets its own near weight plus the far weight of G's record (G's d is 1 - d)
+    dG_own = (1 - d) / (1 + (1 - d))
+    dG_far = (1 - (1 - d)) / (1 + (1 - d))
+    expP = 1.0 + wn * (-1.0) + dG_far * (-1.0)
+    expG = 1.0 + dG_own * (-1.0) + wf * (-1.0)
+    assert np.allclose(o[:N][x == 4], expP) and np.allclose(o[:N][x == 5], expG)
+    assert np.allclose(o[:N][(x != 4) & (x != 5)], 1.0)
+
+
+def test_deadend_filter_cancels_forcing():
+    # a 1-cell slot: cell 4 in x is boxed by walls on -x,+x,-y,+y,-z (5 cut links)
+    n = 9
+    walls = []
+    lo, hi = -40.0, 120.0     # right triangles whose legs span the whole cross-section
+    walls += [[[4.2, lo, lo], [4.2, hi, lo], [4.2, lo, hi]]]       # x = 4.2
+    walls += [[[4.8, lo, lo], [4.8, hi, lo], [4.8, lo, hi]]]       # x = 4.8
+    walls += [[[lo, 4.3, lo], [lo, 4.3, hi], [hi, 4.3, lo]]]       # y = 4.3
+    walls += [[[lo, 4.7, lo], [lo, 4.7, hi], [hi, 4.7, lo]]]       # y = 4.7
+    walls += [[[lo, lo, 4.2], [hi, lo, 4.2], [lo, hi, 4.2]]]       # z = 4.2
+    tri = np.array(walls, np.float32)
+    for on in (0, 1):
+        case = oracle.Case(n, n, n, bc=SLIPBOX, deadend_on=on)
+        case.set_geometry(tri)
+        P = 4 + n * (4 + n * 4)
+        assert bin(int(case.flags[P]) & 63).count("1") == 5
+        u = np.ones(3 * case.N)
+        o, _ = case.forcing(u)
+        changed = o[P] != 1.0
+        assert changed == (on == 0)
+
+
+# --------------------------------------------------------------------------------------------------
+# Forces (Eq. force)
+
+def test_forces_constant_pressure_and_archimedes():
+    n = 24
+    R = 6.2
+    c = (12.1, 11.9, 12.05)
+    tri = W.icosphere(4, R, c)
+    case = oracle.Case(n, n, n)
+    x = centres(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    inside = ((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 < R ** 2).reshape(-1)
+    out = case.forces(tri, np.full(n ** 3, 3.0))
+    assert np.allclose(out[:3], 0.0, atol=1e-10) and out[3] == len(tri)
+    p = np.where(inside, 3.0, 3.0 + 0 * X.reshape(-1))
+    out = case.forces(tri, p)
+    assert np.allclose(out[:3], 0.0, atol=1e-9)
+    # p = x outside and a uniform value inside: F = -(volume) e_x (Archimedes), discretisation-limited
+    p = np.where(inside, 0.0, X.reshape(-1))
+    out = case.forces(tri, p)
+    V = 4.0 / 3.0 * np.pi * R ** 3
+    assert out[0] == pytest.approx(-V, rel=0.06)
+    assert abs(out[1]) < 0.03 * V and abs(out[2]) < 0.03 * V
