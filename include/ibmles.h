@@ -1,0 +1,189 @@
+/* ibmles.h -- C ABI of the GB300 (sm_103a) topology-free immersed-boundary LES library.
+ *
+ * The library implements one fractional time step of the immersed-boundary LES of Onishi & Tsubokura
+ * (arXiv 2002.06206) on a uniform Cartesian grid, plus the per-geometry fluid/solid classification of
+ * a raw triangle soup, as hand-written CUDA kernels.  Every pointer named d_* is a device pointer
+ * owned by the caller; `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * All calls are asynchronous on `stream` unless their comment names a host synchronisation.
+ *
+ * Layout conventions (shared by every call):
+ *   grid      nx*ny*nz cells of size dx; cell (i,j,k) has index c = i + nx*(j + ny*k) and its centre
+ *             at ((i+1/2)dx, (j+1/2)dx, (k+1/2)dx).  At most 2^31/3 cells.
+ *   cell      fields are component-major: u[comp*N + c] (comp 0,1,2 = x,y,z).
+ *   face      fields are one concatenated vector Ux | Uy | Uz of length
+ *             NF = (nx+1)ny nz + nx(ny+1)nz + nx ny(nz+1); Ux index i + (nx+1)(j + ny k) is the face at
+ *             x = i dx, Uy index i + nx(j + (ny+1)k), Uz index i + nx(j + ny k).
+ *   soup      float32 [ntri][3][3] vertex coordinates in grid units (position / dx), no connectivity.
+ *   flags     one byte per cell: bits 0-5 = cut link towards -x,+x,-y,+y,-z,+z; bit 6 = Omega_inc
+ *             (the cell has a cut link); bit 7 = Omega_adj (not Omega_inc, next to an Omega_inc cell).
+ *   face id   a cut face between cell c and c + e_a has id a*N + c.
+ *   precision IBM_FP64: cell/face fields and H are double.  IBM_FP32_REFINE64: they are float; the
+ *             pressure p and the right-hand side b are double in both modes.
+ *
+ * Errors: every int-returning call returns an ibm_status; ibm_last_error() describes the last
+ * failure of the calling thread.  No call aborts or traps on bad input.
+ */
+#ifndef IBMLES_H
+#define IBMLES_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IBM_OK = 0,
+    IBM_E_INVALID = 1,    /* bad argument (null pointer, size, mode, unsupported grid) */
+    IBM_E_NOMEM = 2,      /* device allocation failed */
+    IBM_E_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    IBM_E_NOCONV = 4,     /* the pressure solve hit max_iter; the best iterate is left in p */
+    IBM_E_NONFINITE = 5,  /* a residual norm became NaN or Inf */
+    IBM_E_CAPACITY = 6    /* the cut-face buffer is too small; *n_cut holds the required size */
+} ibm_status;
+
+enum { IBM_BC_PERIODIC = 0, IBM_BC_INFLOW = 1, IBM_BC_OUTFLOW = 2, IBM_BC_SLIP = 3, IBM_BC_NOSLIP = 4 };
+enum { IBM_FP64 = 0, IBM_FP32_REFINE64 = 1 };
+enum { IBM_SOLVER_CG = 0, IBM_SOLVER_BICGSTAB = 1, IBM_SOLVER_RBSOR = 2 };
+
+typedef struct { int32_t nx, ny, nz, reserved; double dx; } ibm_grid;
+
+typedef struct {
+    double eps_edge;     /* edge tolerance of the ray/triangle predicate, relative to |W| (1e-9) */
+    double eps_det;      /* determinant threshold: |W| <= eps_det is "parallel" (0) */
+    int32_t deadend_on;  /* dead-end filter of the IB forcing (Sec. 3.4, Eq. deadend_filter) */
+    int32_t reserved;
+} ibm_geom_params;
+
+typedef struct {
+    double nu;           /* kinematic viscosity (1/Re in non-dimensional units) */
+    double dt;           /* time step */
+    double u_in[3];      /* inflow velocity (Dirichlet faces of type IBM_BC_INFLOW) */
+    int32_t bc[6];       /* domain-face types, order x-, x+, y-, y+, z-, z+ (periodic must pair) */
+    int32_t csm_on;      /* coherent-structure eddy viscosity (Sec. 2.3) */
+    int32_t forcing_on;  /* distributed direct forcing (Sec. 2.1/2.4.2) */
+    int32_t precision;   /* IBM_FP64 or IBM_FP32_REFINE64 */
+    int32_t solver;      /* IBM_SOLVER_* for the pressure Poisson equation */
+    double tol;          /* stop at ||b - A p||_2 <= tol ||b||_2 */
+    int32_t max_iter;    /* cap on Krylov (or SOR) iterations per solve, summed over refinements */
+    int32_t check_every; /* iterations between host reads of the residual (0 = 16) */
+    double inner_tol;    /* FP32 inner solve: relative reduction per FP64 refinement (0 = 1e-4) */
+    double sor_omega;    /* over-relaxation factor of red-black SOR (0 = 1.9) */
+} les_params;
+
+typedef struct {
+    int32_t iters;       /* inner iterations of the last pressure solve */
+    int32_t outer;       /* FP64 refinement passes of the last pressure solve */
+    int32_t status;      /* ibm_status of the solve */
+    int32_t reserved;
+    double relres;       /* ||b - A p|| / ||b|| at exit, computed in FP64 */
+    double bnorm;        /* ||b||_2 */
+    double fsum[3];      /* momentum added by the IB forcing this step: sum of du * dx^3 */
+} les_stats;
+
+typedef struct ibm_geom ibm_geom;
+typedef struct les_state les_state;
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Geometry: classification (Sec. 2.4.1: ray tracing from the cell centres along the grid lines,    */
+/* Moller-Trumbore with a determinant tolerance).                                                   */
+
+/* Device workspace ibm_classify needs for this grid and soup size (bytes). */
+size_t ibm_classify_workspace_bytes(const ibm_grid* grid, int64_t ntri);
+
+/* For each axis a and each grid line through cell centres parallel to a, decide with an exactly
+ * specified FP64 predicate which triangles of d_tri cross it; a crossing at x_hit belongs to the
+ * interior face f = floor(x_hit/dx - 1/2) at position t = x_hit/dx - 1/2 - f in [0,1) along the
+ * centre-to-centre segment.  Writes d_flags bits 0-5 (bits 6-7 cleared) and the cut-face list sorted
+ * by face id with t_lo = min t, t_hi = max t per face.  d_flags[N], d_face_id/d_t_lo/d_t_hi[cap].
+ * Host synchronisation: reads the cut count back; *n_cut (host) = number of cut faces.  Returns
+ * IBM_E_CAPACITY if *n_cut > cap (then only the first cap entries are written; call again with a
+ * buffer of *n_cut).  Triangles with non-finite vertices are skipped.  d_workspace must hold ibm_classify_workspace_bytes() bytes.
+ * *n_tests (host, may be NULL) = number of (triangle, grid line) predicate evaluations. */
+int ibm_classify(const ibm_grid* grid, const float* d_tri, int64_t ntri, const ibm_geom_params* gp,
+                 uint8_t* d_flags, int64_t* d_face_id, double* d_t_lo, double* d_t_hi, int64_t cap,
+                 int64_t* n_cut, int64_t* n_tests, void* d_workspace, size_t ws_bytes, void* stream);
+
+/* Setup (Sec. 2.4.1 Eq. dummy_cell_region, Sec. 2.4.2 Eq. q_axis and Eq. distribution_function):
+ * sets flags bits 6-7 in place and builds two link records per cut face (one per side) with the
+ * ghost branch, its coefficients and the forcing weights.  The returned geometry owns its device
+ * memory; d_flags must stay alive and unchanged while the geometry is used. */
+int ibm_setup(const ibm_grid* grid, const ibm_geom_params* gp, uint8_t* d_flags,
+              const int64_t* d_face_id, const double* d_t_lo, const double* d_t_hi, int64_t n_cut,
+              ibm_geom** out, void* stream);
+int ibm_geom_info(const ibm_geom* geom, int64_t* n_rec, int64_t* n_inc);
+/* Copy the records out: d_idx[n_rec][6] = cell, far, opp, axis, side, branch; d_coef[n_rec][6] =
+ * d/dx, c_ib, c_p, c_o, w_near, w_far; d_cellrec[N] = first record of each cell or -1. */
+int ibm_geom_export(const ibm_geom* geom, int64_t* d_idx, double* d_coef, int64_t* d_cellrec,
+                    void* stream);
+/* Wall velocity u_IB per record (d_uib[n_rec][3], double); NULL resets it to zero. */
+int ibm_set_boundary_velocity(ibm_geom* geom, const double* d_uib, void* stream);
+void ibm_geom_destroy(ibm_geom* geom);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Flow solver.  les_create allocates every workspace once; no later call allocates. `geom` may be  */
+/* NULL (no immersed body); it must outlive the state.                                             */
+
+int les_create(const ibm_grid* grid, const les_params* params, const ibm_geom* geom, les_state** out);
+void les_destroy(les_state* st);
+
+/* Face velocity from a cell field with the face rule of les_faces (no mass correction skipped). */
+int les_init_faces(les_state* st, const void* d_u, void* d_U, void* stream);
+
+/* One fractional step (Sec. 2.1 with Adams-Bashforth 2): CSM eddy viscosity, predictor, IB forcing,
+ * face velocities, RHS, pressure solve, correction.  In/out: d_u[3N], d_U[NF], d_p[N] (double; x0
+ * of the solve), d_H[3N] (holds H^{n-1} on entry and H^n on exit).  first_step != 0 takes an Euler
+ * step.  Host synchronisation: the pressure solve reads its residual every check_every iterations.
+ * `stats` (host, may be NULL) receives the solve's figures. */
+int les_step(les_state* st, void* d_u, void* d_U, double* d_p, void* d_H, int32_t first_step,
+             les_stats* stats, void* stream);
+
+/* The step's operators, exposed one by one (les_step calls exactly these). */
+/* Eq. Smagorinsky/Q/FCS: nu_t per cell from central velocity gradients (ghost values on cut links). */
+int les_csm(les_state* st, const void* d_u, void* d_nut, void* stream);
+/* Predictor: H = -div(U u) + div((nu + nu_t) grad u) + div(nu_t grad u^T); u* = u + dt(3/2 H - 1/2 Hprev). */
+int les_predict(les_state* st, const void* d_u, const void* d_U, const void* d_nut,
+                const void* d_Hprev, void* d_H, void* d_ustar, int32_t first_step, void* stream);
+/* Eq. forcing_term + Eq. discrete_forcing_term: in-place forcing of d_ustar; fsum (host, may be
+ * NULL, synchronises) = momentum added, sum of du * dx^3. */
+int les_forcing(les_state* st, void* d_ustar, double* fsum, void* stream);
+/* Face velocities U* of the intermediate field, outflow faces shifted to zero net boundary flux. */
+int les_faces(les_state* st, const void* d_ustar, void* d_Ustar, void* stream);
+/* Eq. poisson right-hand side b = div(U*)/dt (double). */
+int les_rhs(les_state* st, const void* d_Ustar, double* d_b, void* stream);
+/* Eq. correction: cell velocity from the central pressure gradient, face velocity from the compact one. */
+int les_correct(les_state* st, const void* d_ustar, const void* d_Ustar, const double* d_p,
+                void* d_u, void* d_U, void* stream);
+
+/* Eq. poisson operator in FP64: (A p)_c = sum over uncut links of (p_n - p_c)/dx^2, outflow faces
+ * p = 0, cut links, walls and inflow faces Neumann. */
+int poisson_apply(les_state* st, const double* d_p, double* d_Ap, void* stream);
+/* Solve A p = b to ||b - A p|| <= tol ||b|| with x0 = d_p (in/out).  solver = IBM_SOLVER_*; in
+ * FP32_REFINE64 mode the Krylov iterations run in FP32 inside FP64 iterative refinement.
+ * Host synchronisation as les_step.  Returns IBM_E_NOCONV after max_it iterations. */
+int poisson_solve(les_state* st, const double* d_b, double* d_p, double tol, int32_t max_it,
+                  int32_t solver, les_stats* stats, void* stream);
+
+/* Eq. force: Shepard inverse-distance pressure on the front/back of every triangle,
+ * F = sum_tri area (p_back - p_front) n.  out (host) = {Fx, Fy, Fz, triangles used}; synchronises. */
+int forces(les_state* st, const float* d_tri, int64_t ntri, const double* d_p, double out[4],
+           void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around each kernel group of
+ * les_step / poisson_solve.  les_profile(st, 1) enables and resets the counters, (st, 0) disables.
+ * les_profile_read (synchronises) fills ms[10] (total milliseconds) and launches[10] per group, in
+ * the order: csm, predict, forcing, faces, rhs, residual, cg_dir_spmv, cg_update, correct, sor. */
+int les_profile(les_state* st, int32_t on);
+int les_profile_read(les_state* st, double* ms, int64_t* launches);
+/* Kernels this state launched since les_create or the last les_profile(st, 1) (host counter). */
+int64_t les_kernel_launches(const les_state* st);
+
+/* Number of faces NF of the concatenated face vector for this grid (-1 for an invalid grid). */
+int64_t les_num_faces(const ibm_grid* grid);
+
+const char* ibm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,542 @@
+// les.cu -- the per-step stencil kernels of the immersed-boundary LES (Sec. 2.1-2.4): CSM eddy
+// viscosity, AB2 momentum predictor, distributed direct forcing, face velocities, Poisson right-hand
+// side, velocity correction, and the Shepard surface force.
+//
+// All cell kernels use the same launch shape: a 32 x 8 thread tile over (x, y), each thread marching
+// along z over a chunk of planes, so consecutive threads touch consecutive cells (coalesced rows) and
+// the y/z neighbours of a tile are re-read from L1/L2 rather than HBM.
+#include "solver.cuh"
+
+namespace {
+
+template <class T>
+__device__ __forceinline__ void grad_at(const Dom& D, const T* __restrict__ u, long long P, const int x[3],
+                                        unsigned fl, T inv2dx, T G[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const T up = vel_across(D, u, b, P, x[a], fl, a, +1);
+            const T um = vel_across(D, u, b, P, x[a], fl, a, -1);
+            G[a][b] = (up - um) * inv2dx;
+        }
+}
+
+__device__ __forceinline__ unsigned flags_at(const Dom& D, long long P) { return D.flags ? (unsigned)D.flags[P] : 0u; }
+
+// Eq. Smagorinsky with the coherent-structure coefficient of Eq. Q / Eq. FCS.
+template <class T>
+__global__ void __launch_bounds__(256) k_csm(Dom D, const T* __restrict__ u, T* __restrict__ nut, int kchunk) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+    if (i >= D.nx || j >= D.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    const T inv2dx = (T)(0.5 / D.dx), delta2 = (T)(D.dx * D.dx);
+    for (int k = k0; k < k1; ++k) {
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        const unsigned fl = flags_at(D, P);
+        const int x[3] = {i, j, k};
+        T G[3][3];
+        grad_at(D, u, P, x, fl, inv2dx, G);
+        T SS = 0, WW = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const T S = (T)0.5 * (G[a][b] + G[b][a]);
+                const T W = (T)0.5 * (G[a][b] - G[b][a]);
+                SS += S * S;
+                WW += W * W;
+            }
+        const T Q = (T)0.5 * (WW - SS), E = (T)0.5 * (WW + SS);
+        const T F = E > (T)0 ? Q / E : (T)0;
+        const T aF = F < (T)0 ? -F : F;
+        const T C = (T)(1.0 / 20.0) * (aF * sqrt(aF));
+        nut[P] = C * delta2 * sqrt(SS);
+    }
+}
+
+// Momentum predictor: flux-form central advection with the face velocity U, diffusion with
+// nu + nu_t, the transpose part of the SGS stress divergence, Adams-Bashforth 2 in time.
+template <class T>
+__global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
+                                                 const T* __restrict__ nut, const T* Hprev, T* H,
+                                                 T* __restrict__ ustar, T nu, T dt, int first, int kchunk) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+    if (i >= D.nx || j >= D.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
+    const int n[3] = {D.nx, D.ny, D.nz};
+    for (int k = k0; k < k1; ++k) {
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        const unsigned fl = flags_at(D, P);
+        const int x[3] = {i, j, k};
+        T GP[3][3];
+        grad_at(D, u, P, x, fl, inv2dx, GP);
+        const T nutP = nut[P];
+        T h[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int s = -1; s <= 1; s += 2) {
+                const int fx0 = x[0] + (a == 0 && s > 0), fx1 = x[1] + (a == 1 && s > 0), fx2 = x[2] + (a == 2 && s > 0);
+                const T Uf = U[F.index(a, fx0, fx1, fx2)];
+                const int bit = 2 * a + (s > 0);
+                long long off = 0;
+                const bool interior = !(fl & (1u << bit)) && nb_offset(D, a, s, x[a], off);
+                T nutf = nutP;
+                T GN[3] = {0, 0, 0};
+                if (interior) {
+                    const long long Nn = P + off;
+                    nutf = (T)0.5 * (nutP + nut[Nn]);
+                    int xn[3] = {x[0], x[1], x[2]};
+                    xn[a] += s;
+                    if (xn[a] < 0) xn[a] += n[a];
+                    if (xn[a] >= n[a]) xn[a] -= n[a];
+                    const unsigned fln = flags_at(D, Nn);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (q == a) continue;
+                        GN[q] = (vel_across(D, u, a, Nn, xn[q], fln, q, +1) - vel_across(D, u, a, Nn, xn[q], fln, q, -1)) * inv2dx;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T uP = u[c * D.N + P];
+                    const T uN = vel_across(D, u, c, P, x[a], fl, a, s);
+                    const T D1 = (uN - uP) * invdx;
+                    T Tt;
+                    if (c == a) Tt = D1;
+                    else if (interior) Tt = (T)s * (T)0.5 * (GP[c][a] + GN[c]);
+                    else Tt = (T)s * GP[c][a];
+                    const T conv = -(T)s * Uf * (T)0.5 * (uP + uN);
+                    h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
+                }
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long o = c * D.N + P;
+            const T hc = h[c] * invdx;
+            const T uP = u[o];
+            const T hp = first ? (T)0 : Hprev[o];
+            H[o] = hc;
+            ustar[o] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
+        }
+    }
+}
+
+// Distributed direct forcing, gathered per Omega_inc cell: its own records (near weight) and the
+// records of the cells behind its cut links that point back at it (far weight).  All reads use the
+// unforced u*, so the result does not depend on thread order.
+template <class T>
+__global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __restrict__ inc, long long n_inc,
+                                                        const T* __restrict__ us, double* __restrict__ delta, T dt,
+                                                        int deadend_on, double vol, double* partials,
+                                                        unsigned* counter, double* fscal) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n_inc; q += (long long)gridDim.x * blockDim.x) {
+        const long long X = inc[q];
+        const unsigned fl = D.flags[X];
+        T d3[3] = {0, 0, 0};
+        const bool dead = deadend_on && __popc(fl & 63u) >= 5;
+        if (!dead) {
+            for (int bit = 0; bit < 6; ++bit) {
+                if (!((fl >> bit) & 1u)) continue;
+                const LinkRec& r = link_record(D, X, fl, bit);
+                const long long G = r.far;
+                const T d = (T)r.d, wn = (T)r.w_near;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T uX = ((T)1 - d) * us[c * D.N + X] + d * us[c * D.N + G];
+                    const T Fc = ((T)r.uib[c] - uX) / dt;
+                    d3[c] += dt * wn * Fc;
+                }
+                const unsigned flG = D.flags[G];
+                const int back = bit ^ 1;                  // the same link seen from G
+                const LinkRec& r2 = link_record(D, G, flG, back);
+                const T d2 = (T)r2.d, wf = (T)r2.w_far;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T uX = ((T)1 - d2) * us[c * D.N + G] + d2 * us[c * D.N + X];
+                    const T Fc = ((T)r2.uib[c] - uX) / dt;
+                    d3[c] += dt * wf * Fc;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            delta[3 * q + c] = (double)d3[c];
+            acc[c] += (double)d3[c] * vol;
+        }
+    }
+    grid_reduce<3>(acc, partials, counter, [&](double* tot) {
+        fscal[0] = tot[0];
+        fscal[1] = tot[1];
+        fscal[2] = tot[2];
+    });
+}
+
+template <class T>
+__global__ void k_forcing_apply(Dom D, const int32_t* __restrict__ inc, long long n_inc, const double* __restrict__ delta,
+                                T* __restrict__ us) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n_inc; q += (long long)gridDim.x * blockDim.x) {
+        const long long X = inc[q];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) us[c * D.N + X] = us[c * D.N + X] + (T)delta[3 * q + c];
+    }
+}
+
+__device__ __forceinline__ void face_coords(const FaceLayout& F, int a, long long idx, int x[3]) {
+    x[0] = (int)(idx % F.dim[a][0]);
+    long long t = idx / F.dim[a][0];
+    x[1] = (int)(t % F.dim[a][1]);
+    x[2] = (int)(t / F.dim[a][1]);
+}
+
+__device__ __forceinline__ long long cell_of(const Dom& D, const int x[3]) {
+    return x[0] + (long long)D.sy * x[1] + D.sz * x[2];
+}
+
+// Face velocity of the intermediate field on the faces of axis a.
+template <class T>
+__global__ void k_faces(Dom D, FaceLayout F, int a, const T* __restrict__ us, T* __restrict__ Us) {
+    const long long nf = (long long)F.dim[a][0] * F.dim[a][1] * F.dim[a][2];
+    const int na = a == 0 ? D.nx : (a == 1 ? D.ny : D.nz);
+    const long long st = a == 0 ? 1 : (a == 1 ? (long long)D.sy : D.sz);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nf; idx += (long long)gridDim.x * blockDim.x) {
+        int x[3];
+        face_coords(F, a, idx, x);
+        const int f = x[a];
+        T v;
+        if (f > 0 && f < na) {
+            const long long R = cell_of(D, x), L = R - st;
+            const bool cut = D.flags && ((D.flags[L] >> (2 * a + 1)) & 1u);
+            v = cut ? (T)0 : (T)0.5 * (us[a * D.N + L] + us[a * D.N + R]);
+        } else {
+            const int s = f == 0 ? -1 : 1;
+            const int bc = D.bc[2 * a + (s > 0)];
+            int xi[3] = {x[0], x[1], x[2]};
+            if (bc == IBM_BC_PERIODIC) {
+                xi[a] = na - 1;
+                const long long L = cell_of(D, xi);
+                xi[a] = 0;
+                const long long R = cell_of(D, xi);
+                v = (T)0.5 * (us[a * D.N + L] + us[a * D.N + R]);
+            } else if (bc == IBM_BC_INFLOW) {
+                v = (T)D.u_in[a];
+            } else if (bc == IBM_BC_OUTFLOW) {
+                xi[a] = f == 0 ? 0 : na - 1;
+                v = us[a * D.N + cell_of(D, xi)];
+            } else {
+                v = (T)0;
+            }
+        }
+        Us[F.off[a] + idx] = v;
+    }
+}
+
+// Net boundary flux: fscal[3] = outward flux of inflow faces, fscal[4] = of outflow faces,
+// fscal[5] = number of outflow faces.
+template <class T>
+__global__ void k_boundary_flux(Dom D, FaceLayout F, const T* __restrict__ Us, double* partials, unsigned* counter,
+                                double* fscal) {
+    const int n[3] = {D.nx, D.ny, D.nz};
+    long long plane[6], tot = 0;
+    for (int p = 0; p < 6; ++p) {
+        const int a = p >> 1;
+        plane[p] = (long long)n[(a + 1) % 3] * n[(a + 2) % 3];
+        tot += plane[p];
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        int p = 0;
+        long long r = g;
+        while (r >= plane[p]) r -= plane[p++];
+        const int bc = D.bc[p];
+        if (bc != IBM_BC_INFLOW && bc != IBM_BC_OUTFLOW) continue;
+        const int a = p >> 1, s = (p & 1) ? 1 : -1;
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        int x[3];
+        x[b] = (int)(r % n[b]);
+        x[c] = (int)(r / n[b]);
+        x[a] = s < 0 ? 0 : n[a];
+        const double v = (double)Us[F.index(a, x[0], x[1], x[2])];
+        if (bc == IBM_BC_INFLOW) acc[0] += s * v;
+        else { acc[1] += s * v; acc[2] += 1.0; }
+    }
+    grid_reduce<3>(acc, partials, counter, [&](double* t) {
+        fscal[3] = t[0];
+        fscal[4] = t[1];
+        fscal[5] = t[2];
+    });
+}
+
+template <class T>
+__global__ void k_outflow_shift(Dom D, FaceLayout F, T* __restrict__ Us, const double* __restrict__ fscal) {
+    const double nout = fscal[5];
+    if (nout == 0.0) return;
+    const double shift = (-fscal[3] - fscal[4]) / nout;
+    const int n[3] = {D.nx, D.ny, D.nz};
+    for (int p = 0; p < 6; ++p) {
+        if (D.bc[p] != IBM_BC_OUTFLOW) continue;
+        const int a = p >> 1, s = (p & 1) ? 1 : -1;
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const long long np = (long long)n[b] * n[c];
+        for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < np; r += (long long)gridDim.x * blockDim.x) {
+            int x[3];
+            x[b] = (int)(r % n[b]);
+            x[c] = (int)(r / n[b]);
+            x[a] = s < 0 ? 0 : n[a];
+            const long long fi = F.index(a, x[0], x[1], x[2]);
+            Us[fi] = (T)((double)Us[fi] + s * shift);
+        }
+    }
+}
+
+// Eq. poisson right-hand side: b = div(U*) / dt, evaluated in FP64.
+template <class T>
+__global__ void __launch_bounds__(256) k_rhs(Dom D, FaceLayout F, const T* __restrict__ Us, double* __restrict__ b,
+                                             double inv_dxdt, int kchunk) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+    if (i >= D.nx || j >= D.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    const double dxdt = 1.0 / inv_dxdt;
+    for (int k = k0; k < k1; ++k) {
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        double div = 0.0;
+        div += (double)Us[F.index(0, i + 1, j, k)] - (double)Us[F.index(0, i, j, k)];
+        div += (double)Us[F.index(1, i, j + 1, k)] - (double)Us[F.index(1, i, j, k)];
+        div += (double)Us[F.index(2, i, j, k + 1)] - (double)Us[F.index(2, i, j, k)];
+        b[P] = div / dxdt;
+    }
+}
+
+// Eq. correction on the cells: central pressure gradient through the link values.
+template <class T>
+__global__ void __launch_bounds__(256) k_correct_cells(Dom D, const T* __restrict__ us, const double* __restrict__ p,
+                                                       T* __restrict__ u, double dt, int kchunk) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+    if (i >= D.nx || j >= D.ny) return;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    const double twodx = 2.0 * D.dx;
+    for (int k = k0; k < k1; ++k) {
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        const unsigned fl = flags_at(D, P);
+        const int x[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double pp = p_across(D, p, P, x[a], fl, a, +1);
+            const double pm = p_across(D, p, P, x[a], fl, a, -1);
+            u[a * D.N + P] = (T)((double)us[a * D.N + P] - dt * (pp - pm) / twodx);
+        }
+    }
+}
+
+// Eq. correction on the faces of axis a: compact pressure difference across the face.
+template <class T>
+__global__ void k_correct_faces(Dom D, FaceLayout F, int a, const T* __restrict__ Us, const double* __restrict__ p,
+                                T* __restrict__ U, double dt) {
+    const long long nf = (long long)F.dim[a][0] * F.dim[a][1] * F.dim[a][2];
+    const int na = a == 0 ? D.nx : (a == 1 ? D.ny : D.nz);
+    const long long st = a == 0 ? 1 : (a == 1 ? (long long)D.sy : D.sz);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nf; idx += (long long)gridDim.x * blockDim.x) {
+        int x[3];
+        face_coords(F, a, idx, x);
+        const int f = x[a];
+        const long long fi = F.off[a] + idx;
+        double pl, pr;
+        if (f > 0 && f < na) {
+            const long long R = cell_of(D, x), L = R - st;
+            if (D.flags && ((D.flags[L] >> (2 * a + 1)) & 1u)) { U[fi] = Us[fi]; continue; }
+            pl = p[L];
+            pr = p[R];
+        } else {
+            const int s = f == 0 ? -1 : 1;
+            const int bc = D.bc[2 * a + (s > 0)];
+            int xi[3] = {x[0], x[1], x[2]};
+            if (bc == IBM_BC_PERIODIC) {
+                xi[a] = na - 1;
+                pl = p[cell_of(D, xi)];
+                xi[a] = 0;
+                pr = p[cell_of(D, xi)];
+            } else if (bc == IBM_BC_OUTFLOW) {
+                xi[a] = f == 0 ? 0 : na - 1;
+                const double pin = p[cell_of(D, xi)];
+                if (s < 0) { pl = -pin; pr = pin; } else { pl = pin; pr = -pin; }
+            } else {
+                U[fi] = Us[fi];
+                continue;
+            }
+        }
+        U[fi] = (T)((double)Us[fi] - dt * (pr - pl) / D.dx);
+    }
+}
+
+// Eq. force: Shepard average of p on each side of every triangle over the 2x2x2 block of cell
+// centres around its centroid.
+__global__ void k_forces(Dom D, const float* __restrict__ tri, long long ntri, const double* __restrict__ p,
+                         double* partials, unsigned* counter, double* out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ntri; t += (long long)gridDim.x * blockDim.x) {
+        double V[3][3];
+        bool ok = true;
+        for (int q = 0; q < 9; ++q) {
+            V[q / 3][q % 3] = (double)tri[9 * t + q];
+            ok = ok && isfinite(V[q / 3][q % 3]);
+        }
+        if (!ok) continue;
+        double e1[3], e2[3], nrm[3], X[3];
+        for (int d = 0; d < 3; ++d) {
+            e1[d] = V[1][d] - V[0][d];
+            e2[d] = V[2][d] - V[0][d];
+            X[d] = (V[0][d] + V[1][d] + V[2][d]) / 3.0;
+        }
+        nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double len = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+        if (!(len > 0.0)) continue;
+        const double area = 0.5 * len * D.dx * D.dx;
+        for (int d = 0; d < 3; ++d) nrm[d] /= len;
+        long long base[3];
+        for (int d = 0; d < 3; ++d) base[d] = (long long)floor(X[d] - 0.5);
+        double sw[2] = {0.0, 0.0}, sp[2] = {0.0, 0.0};
+        const long long n[3] = {D.nx, D.ny, D.nz};
+        for (int dk = 0; dk < 2; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di) {
+                    const long long x[3] = {base[0] + di, base[1] + dj, base[2] + dk};
+                    if (x[0] < 0 || x[1] < 0 || x[2] < 0 || x[0] >= n[0] || x[1] >= n[1] || x[2] >= n[2]) continue;
+                    double r2 = 0.0, sd = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double r = ((double)x[d] + 0.5) - X[d];
+                        r2 += r * r;
+                        sd += nrm[d] * r;
+                    }
+                    if (sd == 0.0) continue;
+                    if (r2 < 1e-24) r2 = 1e-24;
+                    const double w = 1.0 / r2;
+                    const int side = sd > 0.0 ? 0 : 1;
+                    sw[side] += w;
+                    sp[side] += w * p[x[0] + (long long)D.sy * x[1] + D.sz * x[2]];
+                }
+        if (sw[0] == 0.0 || sw[1] == 0.0) continue;
+        const double pf = sp[0] / sw[0], pb = sp[1] / sw[1];
+        for (int d = 0; d < 3; ++d) acc[d] += area * (pb - pf) * nrm[d];
+        acc[3] += 1.0;
+    }
+    grid_reduce<4>(acc, partials, counter, [&](double* t) {
+        for (int q = 0; q < 4; ++q) out[q] = t[q];
+    });
+}
+
+unsigned lin_blocks(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    long long cap = 16LL * IBM_NSM;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
+    if (c.prec == IBM_FP64)
+        k_csm<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, (const double*)u, (double*)nut, c.cg.kchunk);
+    else
+        k_csm<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, (const float*)u, (float*)nut, c.cg.kchunk);
+    IBM_LAUNCHED("k_csm");
+    IBM_COUNT(c, 1);
+    return IBM_OK;
+}
+
+int launch_predict(const LesCtx& c, const void* u, const void* U, const void* nut, const void* Hprev, void* H,
+                   void* ustar, int first, cudaStream_t s) {
+    if (c.prec == IBM_FP64)
+        k_predict<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)u, (const double*)U,
+                                                           (const double*)nut, (const double*)Hprev, (double*)H,
+                                                           (double*)ustar, c.nu, c.dt, first, c.cg.kchunk);
+    else
+        k_predict<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)u, (const float*)U,
+                                                          (const float*)nut, (const float*)Hprev, (float*)H,
+                                                          (float*)ustar, (float)c.nu, (float)c.dt, first,
+                                                          c.cg.kchunk);
+    IBM_LAUNCHED("k_predict");
+    IBM_COUNT(c, 1);
+    return IBM_OK;
+}
+
+int launch_forcing(const LesCtx& c, void* ustar, cudaStream_t s) {
+    if (c.n_inc == 0 || !c.D.flags) {
+        IBM_CUDA(cudaMemsetAsync(c.fscal, 0, 3 * sizeof(double), s));
+        return IBM_OK;
+    }
+    const unsigned nb = lin_blocks(c.n_inc, 256);
+    const double vol = c.D.dx * c.D.dx * c.D.dx;
+    if (c.prec == IBM_FP64) {
+        k_forcing_gather<double><<<nb, 256, 0, s>>>(c.D, c.inc, c.n_inc, (const double*)ustar, c.fdelta, c.dt,
+                                                    c.deadend_on, vol, c.partials, c.counter, c.fscal);
+        k_forcing_apply<double><<<nb, 256, 0, s>>>(c.D, c.inc, c.n_inc, c.fdelta, (double*)ustar);
+    } else {
+        k_forcing_gather<float><<<nb, 256, 0, s>>>(c.D, c.inc, c.n_inc, (const float*)ustar, c.fdelta, (float)c.dt,
+                                                   c.deadend_on, vol, c.partials, c.counter, c.fscal);
+        k_forcing_apply<float><<<nb, 256, 0, s>>>(c.D, c.inc, c.n_inc, c.fdelta, (float*)ustar);
+    }
+    IBM_LAUNCHED("k_forcing");
+    IBM_COUNT(c, 2);
+    return IBM_OK;
+}
+
+template <class T>
+static void faces_t(const LesCtx& c, const T* us, T* Us, cudaStream_t s) {
+    for (int a = 0; a < 3; ++a) {
+        const long long nf = (long long)c.F.dim[a][0] * c.F.dim[a][1] * c.F.dim[a][2];
+        k_faces<T><<<lin_blocks(nf, 256), 256, 0, s>>>(c.D, c.F, a, us, Us);
+    }
+    k_boundary_flux<T><<<64, 256, 0, s>>>(c.D, c.F, Us, c.partials, c.counter, c.fscal);
+    k_outflow_shift<T><<<64, 256, 0, s>>>(c.D, c.F, Us, c.fscal);
+}
+
+int launch_faces(const LesCtx& c, const void* ustar, void* Ustar, cudaStream_t s) {
+    if (c.prec == IBM_FP64) faces_t<double>(c, (const double*)ustar, (double*)Ustar, s);
+    else faces_t<float>(c, (const float*)ustar, (float*)Ustar, s);
+    IBM_LAUNCHED("k_faces");
+    IBM_COUNT(c, 5);
+    return IBM_OK;
+}
+
+int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s) {
+    const double inv = 1.0 / (c.D.dx * c.dt);
+    if (c.prec == IBM_FP64)
+        k_rhs<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)Ustar, b, inv, c.cg.kchunk);
+    else
+        k_rhs<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)Ustar, b, inv, c.cg.kchunk);
+    IBM_LAUNCHED("k_rhs");
+    IBM_COUNT(c, 1);
+    return IBM_OK;
+}
+
+template <class T>
+static void correct_t(const LesCtx& c, const T* us, const T* Us, const double* p, T* u, T* U, cudaStream_t s) {
+    k_correct_cells<T><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, us, p, u, c.dt, c.cg.kchunk);
+    for (int a = 0; a < 3; ++a) {
+        const long long nf = (long long)c.F.dim[a][0] * c.F.dim[a][1] * c.F.dim[a][2];
+        k_correct_faces<T><<<lin_blocks(nf, 256), 256, 0, s>>>(c.D, c.F, a, Us, p, U, c.dt);
+    }
+}
+
+int launch_correct(const LesCtx& c, const void* ustar, const void* Ustar, const double* p, void* u, void* U,
+                   cudaStream_t s) {
+    if (c.prec == IBM_FP64)
+        correct_t<double>(c, (const double*)ustar, (const double*)Ustar, p, (double*)u, (double*)U, s);
+    else
+        correct_t<float>(c, (const float*)ustar, (const float*)Ustar, p, (float*)u, (float*)U, s);
+    IBM_LAUNCHED("k_correct");
+    IBM_COUNT(c, 4);
+    return IBM_OK;
+}
+
+int launch_forces(const LesCtx& c, const float* tri, long long ntri, const double* p, double* d_out4, cudaStream_t s) {
+    k_forces<<<lin_blocks(ntri, 128), 128, 0, s>>>(c.D, tri, ntri, p, c.partials, c.counter, d_out4);
+    IBM_LAUNCHED("k_forces");
+    IBM_COUNT(c, 1);
+    return IBM_OK;
+}

@@ -1,0 +1,339 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on seeded synthetic inputs.
+
+Bars: flags, cut faces, t_lo/t_hi and link records bit-exact; single operators rel L2 <= 1e-12 in
+FP64 and <= 2e-5 in FP32 (relative to the scale of the operator's terms where the output cancels);
+pressure residual ||b - A p|| / ||b|| <= tol evaluated by the oracle; velocity rel L2 <= 1e-4 after 10
+steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+CHANNEL = (1, 2, 3, 3, 3, 3)
+GROUND = (1, 2, 3, 3, 4, 3)
+PER = (0, 0, 0, 0, 0, 0)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2002_06206_gb300 import build
+    build.build()
+    from paper_2002_06206_gb300 import ibmles
+    ibmles.lib()
+    return ibmles
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
+
+
+def both_geometries(L, nx, ny, nz, tri, bc=CHANNEL, nu=0.05, dt=0.2, deadend=0, eps_edge=1e-9):
+    g = L.make_grid(nx, ny, nz)
+    geo = L.Geometry(g, torch.from_numpy(np.ascontiguousarray(tri, np.float32)).cuda(), eps_edge=eps_edge,
+                     deadend_on=deadend)
+    ref = oracle.Case(nx, ny, nz, 1.0, nu, dt, bc, deadend_on=deadend)
+    ref.set_geometry(tri, eps_edge=eps_edge)
+    return g, geo, ref
+
+
+def assert_geometry_equal(geo, ref):
+    assert np.array_equal(geo.flags.cpu().numpy(), ref.flags)
+    fid, tlo, thi = ref.cut
+    assert geo.n_cut == len(fid)
+    assert np.array_equal(geo.face_id.cpu().numpy(), fid)
+    assert np.array_equal(geo.t_lo.cpu().numpy(), tlo)          # bit-exact FP64
+    assert np.array_equal(geo.t_hi.cpu().numpy(), thi)
+    idx, coef, cellrec = geo.export()
+    r = ref.rec
+    assert geo.n_rec == len(r) and geo.n_inc == len(ref.inc)
+    gi = idx.cpu().numpy()
+    for q, name in enumerate(("cell", "far", "opp", "axis", "side", "branch")):
+        assert np.array_equal(gi[:, q], r[name]), name
+    gc = coef.cpu().numpy()
+    for q, name in enumerate(("d", "c_ib", "c_p", "c_o", "w_near", "w_far")):
+        assert np.array_equal(gc[:, q], r[name]), name
+    assert np.array_equal(cellrec.cpu().numpy(), ref.cellrec)
+
+
+# ------------------------------------------------------------------------------------------------
+# S0 / S1: classification and setup, bit-exact
+
+@pytest.mark.parametrize("name", ["sphere_64x32x32", "dirty_sphere_256x128x128", "cube_plate_512x256x256",
+                                  "vehicle_1024x512x384"])
+def test_geometry_bit_exact_full_configs(L, name):
+    cfg = W.get_config(name)
+    tri = cfg.soup()
+    _, geo, ref = both_geometries(L, cfg.nx, cfg.ny, cfg.nz, tri, cfg.bc, cfg.nu, cfg.dt, cfg.deadend_on)
+    assert_geometry_equal(geo, ref)
+    assert geo.n_tests == ref.n_tests
+
+
+@pytest.mark.parametrize("seed,size", [(1, 0.7), (2, 3.0), (3, 9.0)])
+def test_geometry_bit_exact_random_soup_ragged_grid(L, seed, size):
+    tri = W.random_soup(4000, (-2, -2, -2), (39, 15, 13), size, seed=seed)
+    _, geo, ref = both_geometries(L, 37, 13, 11, tri)
+    assert_geometry_equal(geo, ref)
+
+
+def test_geometry_edge_cases(L):
+    # empty soup, soup outside the domain, non-finite vertices, coplanar triangles, tiny grids
+    g, geo, ref = both_geometries(L, 9, 7, 5, np.zeros((0, 3, 3), np.float32))
+    assert geo.n_cut == 0 and not geo.flags.any()
+    far = W.random_soup(50, (100, 100, 100), (120, 120, 120), 2.0, seed=1)
+    _, geo, ref = both_geometries(L, 9, 7, 5, far)
+    assert geo.n_cut == 0
+    tri = W.random_soup(300, (0, 0, 0), (9, 7, 5), 3.0, seed=4)
+    tri[5, 0, 0] = np.nan
+    tri[9, 2, 1] = np.inf
+    tri[11] = tri[11, 0]                      # degenerate: all three vertices equal
+    _, geo, ref = both_geometries(L, 9, 7, 5, tri)
+    assert_geometry_equal(geo, ref)
+    plane = np.array([[[0.2, 2.5, 0.3], [7.1, 2.5, 0.4], [0.5, 2.5, 4.6]]], np.float32)
+    _, geo, ref = both_geometries(L, 9, 7, 5, plane)
+    assert_geometry_equal(geo, ref)
+    _, geo, ref = both_geometries(L, 1, 1, 1, tri)
+    assert geo.n_cut == 0
+    _, geo, ref = both_geometries(L, 16, 1, 1, W.axis_box((3.3, -1, -1), (9.6, 2, 2)))
+    assert_geometry_equal(geo, ref)
+
+
+def test_classify_capacity_error_reports_required_size(L):
+    import ctypes as C
+    cfg = W.get_config("sphere_64x32x32")
+    tri = torch.from_numpy(cfg.soup()).cuda()
+    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz)
+    lib = L.lib()
+    N = cfg.nx * cfg.ny * cfg.nz
+    flags = torch.empty(N, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(lib.ibm_classify_workspace_bytes(C.byref(g), tri.shape[0]), dtype=torch.uint8, device="cuda")
+    cap = 10
+    fid = torch.empty(cap, dtype=torch.int64, device="cuda")
+    tlo = torch.empty(cap, dtype=torch.float64, device="cuda")
+    thi = torch.empty(cap, dtype=torch.float64, device="cuda")
+    n = C.c_int64()
+    gp = L.GeomParams(1e-9, 0.0, 0, 0)
+    rc = lib.ibm_classify(C.byref(g), C.c_void_p(tri.data_ptr()), tri.shape[0], C.byref(gp),
+                          C.c_void_p(flags.data_ptr()), C.c_void_p(fid.data_ptr()), C.c_void_p(tlo.data_ptr()),
+                          C.c_void_p(thi.data_ptr()), cap, C.byref(n), None, C.c_void_p(ws.data_ptr()),
+                          ws.numel(), None)
+    assert rc == L.E_CAPACITY
+    ref = oracle.Case(cfg.nx, cfg.ny, cfg.nz)
+    ref.classify(cfg.soup())
+    assert n.value == len(ref.cut[0])
+    rc = lib.ibm_classify(C.byref(g), C.c_void_p(tri.data_ptr()), tri.shape[0], C.byref(gp),
+                          C.c_void_p(flags.data_ptr()), C.c_void_p(fid.data_ptr()), None, None, cap, C.byref(n),
+                          None, C.c_void_p(ws.data_ptr()), 16, None)
+    assert rc == L.E_INVALID
+
+
+# ------------------------------------------------------------------------------------------------
+# S2-S6: single operators on identical inputs
+
+def _setup_ops(L, prec, nx=48, ny=40, nz=36, bc=CHANNEL, deadend=0, seed=3):
+    tri = np.concatenate([W.icosphere(3, 7.3, (17.2, 19.6, 18.1)),
+                          W.fan_disk((30.3, 20.1, 17.7), 6.0, 0, 64),
+                          W.random_soup(60, (5, 5, 5), (44, 36, 32), 2.5, seed=seed)]).astype(np.float32)
+    g, geo, ref = both_geometries(L, nx, ny, nz, tri, bc, 0.03, 0.15, deadend)
+    rng = np.random.default_rng(seed)
+    dtype = np.float64 if prec == L.FP64 else np.float32
+    u = (np.array([1.0, 0.0, 0.0])[:, None] + 0.3 * rng.standard_normal((3, ref.N))).astype(dtype)
+    solver = L.Solver(g, 0.03, 0.15, bc, precision=prec, tol=1e-10, geometry=geo)
+    return g, geo, ref, solver, u, rng
+
+
+def _t(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
+def test_single_operators_match_oracle(L, prec, tol):
+    g, geo, ref, solver, u, rng = _setup_ops(L, prec, deadend=1)
+    td = solver.dtype
+    N, NF = ref.N, ref.NF
+    u64 = u.astype(np.float64).reshape(-1)
+    # CSM
+    nut = torch.empty(N, dtype=td, device="cuda")
+    solver.csm(_t(u, td), nut)
+    nut_ref = ref.csm(u64)
+    assert rel(nut.cpu().numpy(), nut_ref) <= tol
+    # faces from u (init rule) and predictor
+    U = torch.empty(NF, dtype=td, device="cuda")
+    solver.init_faces(_t(u, td), U)
+    U_ref = ref.faces(u64)
+    assert rel(U.cpu().numpy(), U_ref) <= tol
+    Hprev = (0.1 * rng.standard_normal(3 * N)).astype(u.dtype)
+    nut_in = nut_ref.astype(u.dtype)
+    U_in = U_ref.astype(u.dtype)
+    H = _t(Hprev, td)
+    us = torch.empty(3 * N, dtype=td, device="cuda")
+    solver.predict(_t(u, td), _t(U_in, td), _t(nut_in, td), H, H, us, False)
+    H_ref, us_ref = ref.predict(u64, U_in.astype(np.float64), nut_in.astype(np.float64),
+                                Hprev.astype(np.float64), False)
+    scale = np.linalg.norm(np.abs(U_in).max() * np.abs(u64)) + np.linalg.norm(H_ref)
+    assert np.linalg.norm(H.cpu().numpy() - H_ref) <= tol * scale
+    assert rel(us.cpu().numpy(), us_ref) <= tol
+    # forcing (dead-end filter on)
+    us_in = us_ref.astype(u.dtype)
+    usg = _t(us_in, td)
+    fs = solver.forcing(usg)
+    us2_ref, fs_ref = ref.forcing(us_in.astype(np.float64))
+    assert rel(usg.cpu().numpy(), us2_ref) <= tol
+    assert np.allclose(fs, fs_ref, rtol=max(tol, 1e-12) * 10, atol=1e-9 * np.abs(fs_ref).max())
+    # faces of u* (with the outflow shift), RHS
+    us2_in = us2_ref.astype(u.dtype)
+    Us = torch.empty(NF, dtype=td, device="cuda")
+    solver.faces(_t(us2_in, td), Us)
+    Us_ref = ref.faces(us2_in.astype(np.float64))
+    assert rel(Us.cpu().numpy(), Us_ref) <= tol
+    Us_in = Us_ref.astype(u.dtype)
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    solver.rhs(_t(Us_in, td), b)
+    b_ref = ref.rhs(Us_in.astype(np.float64))
+    assert rel(b.cpu().numpy(), b_ref) <= 1e-12
+    # operator and correction
+    p = rng.standard_normal(N)
+    Ap = torch.empty(N, dtype=torch.float64, device="cuda")
+    solver.apply(_t(p, torch.float64), Ap)
+    assert rel(Ap.cpu().numpy(), ref.apply(p)) <= 1e-12
+    un = torch.empty(3 * N, dtype=td, device="cuda")
+    Un = torch.empty(NF, dtype=td, device="cuda")
+    solver.correct(_t(us2_in, td), _t(Us_in, td), _t(p, torch.float64), un, Un)
+    un_ref, Un_ref = ref.correct(us2_in.astype(np.float64), Us_in.astype(np.float64), p)
+    assert rel(un.cpu().numpy(), un_ref) <= tol
+    assert rel(Un.cpu().numpy(), Un_ref) <= tol
+
+
+@pytest.mark.parametrize("prec,solver_kind,tol", [(0, 0, 1e-10), (1, 0, 1e-6), (0, 2, 1e-8), (1, 0, 1e-9)])
+def test_poisson_solve_reaches_tolerance(L, prec, solver_kind, tol):
+    g, geo, ref, solver, u, rng = _setup_ops(L, prec)
+    # b in the range of A: sealed pockets (the sphere's interior) are pure-Neumann components, on which
+    # only a right-hand side with zero sum per component has a solution
+    b = ref.apply(rng.standard_normal(ref.N))
+    p0 = rng.standard_normal(ref.N) * 0.1
+    p = _t(p0, torch.float64)
+    st = solver.solve(_t(b, torch.float64), p, tol, 200000, solver_kind)
+    ph = p.cpu().numpy()
+    res = np.linalg.norm(b - ref.apply(ph)) / np.linalg.norm(b)
+    assert st.status == 0 and res <= tol * 1.0001 and abs(st.relres - res) <= 1e-3 * tol + 1e-15
+    # the oracle's BiCGStab solution agrees up to the conditioning of the tolerance
+    pr, _ = ref.solve(b, p0, tol=1e-12)
+    assert rel(ref.apply(ph), ref.apply(pr)) <= 2 * tol
+
+
+def test_poisson_nonconvergence_and_nonfinite_are_reported(L):
+    g, geo, ref, solver, u, rng = _setup_ops(L, 0)
+    b = ref.apply(rng.standard_normal(ref.N))
+    p = torch.zeros(ref.N, dtype=torch.float64, device="cuda")
+    rc, st = solver.solve(_t(b, torch.float64), p, 1e-12, 5, 0, check=False)
+    assert rc == L.E_NOCONV and 5 <= st.iters <= 5 + 16 and np.isfinite(st.relres)
+    assert torch.isfinite(p).all()
+    b[7] = np.nan
+    p.zero_()
+    rc, st = solver.solve(_t(b, torch.float64), p, 1e-8, 100, 0, check=False)
+    assert rc == L.E_NONFINITE
+
+
+# ------------------------------------------------------------------------------------------------
+# Whole steps
+
+def _run_pair(L, cfg_like, tri, steps, prec, tol, u0, bc):
+    nx, ny, nz, nu, dt = cfg_like
+    g, geo, ref = both_geometries(L, nx, ny, nz, tri, bc, nu, dt)
+    solver = L.Solver(g, nu, dt, bc, precision=prec, tol=tol, geometry=geo)
+    st = solver.fields(u0)
+    ost = ref.initial_state(u0)
+    for _ in range(steps):
+        s = solver.step(st)
+        assert s.status == 0 and s.relres <= tol
+        ref.step(ost, tol=tol)
+    torch.cuda.synchronize()
+    return st, ost, ref
+
+
+def test_ten_steps_fp64_sphere_64x32x32(L):
+    cfg = W.get_config("sphere_64x32x32")
+    u0 = W.initial_fields(cfg)
+    st, ost, _ = _run_pair(L, (cfg.nx, cfg.ny, cfg.nz, cfg.nu, cfg.dt), cfg.soup(), 10, L.FP64, 1e-10, u0, cfg.bc)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-8
+    assert rel(st["U"].cpu().numpy(), ost["U"]) <= 1e-8
+
+
+def test_ten_steps_fp32_refine64_dirty_sphere_96x48x48(L):
+    # the dirty-sphere recipe scaled to D = 12 cells so that the oracle finishes in seconds
+    tri = W.dirty_sphere(seed=2, radius=6.0, center=(24.0, 24.0, 24.0), subdiv=4)
+    cfg = (96, 48, 48, 12.0 / 1e4, 0.2)
+    u0 = W.initial_fields(W.Config("d", 96, 48, 48, 0, 0, 0, 0, 0, CHANNEL, seed=2))
+    st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP32_REFINE64, 1e-6, u0, CHANNEL)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-4
+
+
+def test_ten_steps_ground_cube_plate_ragged(L):
+    tri = W.cube_and_plate() * np.float32(0.25)
+    cfg = (131, 64, 37, 8.0 / 4e4, 0.2)
+    u0 = W.initial_fields(W.Config("c", 131, 64, 37, 0, 0, 0, 0, 0, GROUND, seed=3))
+    st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP64, 1e-9, u0, GROUND)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-6
+
+
+def test_taylor_green_periodic_matches_oracle(L):
+    n = 32
+    u0, _, dx = W.taylor_green(n, 0.0, 100.0, nz=2)
+    g = L.make_grid(n, n, 2, dx)
+    solver = L.Solver(g, 0.01, 1e-3, PER, precision=L.FP64, tol=1e-11, csm_on=0, forcing_on=0)
+    ref = oracle.Case(n, n, 2, dx, 0.01, 1e-3, PER, csm_on=0, forcing_on=0)
+    st = solver.fields(u0)
+    ost = ref.initial_state(u0)
+    for _ in range(20):
+        solver.step(st)
+        ref.step(ost, tol=1e-11)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-8
+
+
+def test_full_size_dirty_sphere_step_properties(L):
+    """At the benchmark size (256x128x128, FP32 + FP64 refinement): operator parity on the full grid,
+    and after a full step the pressure residual and the projection identity hold when evaluated by
+    the oracle on the GPU's outputs."""
+    cfg = W.get_config("dirty_sphere_256x128x128")
+    tri = cfg.soup()
+    g, geo, ref = both_geometries(L, cfg.nx, cfg.ny, cfg.nz, tri, cfg.bc, cfg.nu, cfg.dt)
+    solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, precision=L.FP32_REFINE64, tol=cfg.tol, geometry=geo)
+    u0 = W.initial_fields(cfg).astype(np.float32)
+    st = solver.fields(u0)
+    for _ in range(3):
+        solver.step(st)
+    u = st["u"].cpu().numpy().astype(np.float64)
+    nut = torch.empty(ref.N, dtype=torch.float32, device="cuda")
+    solver.csm(st["u"], nut)
+    assert rel(nut.cpu().numpy(), ref.csm(u)) <= 2e-5
+    # one step through the operators, checked by the oracle
+    us = torch.empty(3 * ref.N, dtype=torch.float32, device="cuda")
+    H = st["H"].clone()
+    solver.predict(st["u"], st["U"], nut, H, H, us, False)
+    solver.forcing(us)
+    Us = torch.empty(ref.NF, dtype=torch.float32, device="cuda")
+    solver.faces(us, Us)
+    b = torch.empty(ref.N, dtype=torch.float64, device="cuda")
+    solver.rhs(Us, b)
+    p = st["p"].clone()
+    stats = solver.solve(b, p, cfg.tol)
+    bh, ph = b.cpu().numpy(), p.cpu().numpy()
+    res = bh - ref.apply(ph)
+    assert np.linalg.norm(res) <= cfg.tol * np.linalg.norm(bh) * 1.0001
+    un = torch.empty_like(us)
+    Un = torch.empty_like(Us)
+    solver.correct(us, Us, p, un, Un)
+    Ux, Uy, Uz = oracle.split_faces(Un.cpu().numpy().astype(np.float64), cfg.nx, cfg.ny, cfg.nz)
+    div = (np.diff(Ux, axis=2) + np.diff(Uy, axis=1) + np.diff(Uz, axis=0)).reshape(-1)
+    # FP32 faces: the identity holds to the rounding of the stored face values
+    assert np.abs(div - cfg.dt * res).max() <= 1e-5 * np.abs(Us.cpu().numpy()).max()
+    assert stats.relres <= cfg.tol
