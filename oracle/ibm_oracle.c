@@ -481,33 +481,40 @@ void or_predict(const or_grid* g, const or_params* pr, const uint8_t* flags, con
 /* ------------------------------------------------------------------------------------------------ */
 /* Distributed direct forcing: Eq. forcing_term, Eq. discrete_forcing_term, Eq. distribution_function,*/
 /* dead-end filter Eq. deadend_filter.  Reading: the velocity at the intersection X is the linear     */
-/* interpolant of the background u* between P and G; the force (u_IB - u*_X)/dt is spread to P and G  */
-/* with the printed weights D; all records use the background u*, so the result is order-free.        */
+/* interpolant of the background u* between P and the cell G behind the wall; the force             */
+/* (u_IB - u*_X)/dt is spread with the fluid-side weight d/(dx + d) to P.  The ghost-side weight acts */
+/* on the ghost cell of P's dummy stencil, whose value Eq. q_axis already fixes; G itself belongs to  */
+/* another fluid region and is forced through its own records.  All records use the background u*.  */
 
 void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 int64_t nrec, const double* ustar_in, double* ustar_out, double fsum[3]) {
     const int64_t N = ncells(g);
     const double dt = pr->dt, vol = g->dx * g->dx * g->dx;
     double* delta = (double*)calloc((size_t)(3 * N), sizeof(double));
+    double* wsum = (double*)calloc((size_t)N, sizeof(double));
     fsum[0] = fsum[1] = fsum[2] = 0.0;
     for (int64_t r = 0; r < nrec; ++r) {
         const or_record* R = &rec[r];
         int64_t P = R->cell, G = R->far;
         int dead_P = pr->deadend_on && popcount6(flags[P] & 63) >= 5;
-        int dead_G = pr->deadend_on && popcount6(flags[G] & 63) >= 5;
+        if (!dead_P) wsum[P] += R->w_near;
         for (int i = 0; i < 3; ++i) {
             double uX = (1.0 - R->d) * ustar_in[i * N + P] + R->d * ustar_in[i * N + G];
             double F = (R->uib[i] - uX) / dt;
             if (!dead_P) delta[i * N + P] += dt * R->w_near * F;
-            if (!dead_G) delta[i * N + G] += dt * R->w_far * F;
         }
     }
+    /* Reading: a cell crossed by several IB points receives the sum of their spread forces; where the
+     * printed weights add up to more than 1 the sum is divided by that total, so that the explicit
+     * update stays a relaxation towards u_IB (unnormalised sums over-correct and grow step by step). */
     for (int i = 0; i < 3; ++i)
         for (int64_t P = 0; P < N; ++P) {
-            ustar_out[i * N + P] = ustar_in[i * N + P] + delta[i * N + P];
-            fsum[i] += delta[i * N + P] * vol;
+            double dlt = wsum[P] > 1.0 ? delta[i * N + P] / wsum[P] : delta[i * N + P];
+            ustar_out[i * N + P] = ustar_in[i * N + P] + dlt;
+            fsum[i] += dlt * vol;
         }
     free(delta);
+    free(wsum);
 }
 
 /* ------------------------------------------------------------------------------------------------ */

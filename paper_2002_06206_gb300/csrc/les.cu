@@ -124,9 +124,11 @@ __global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* _
     }
 }
 
-// Distributed direct forcing, gathered per Omega_inc cell: its own records (near weight) and the
-// records of the cells behind its cut links that point back at it (far weight).  All reads use the
-// unforced u*, so the result does not depend on thread order.
+// Distributed direct forcing (Eq. forcing_term, Eq. discrete_forcing_term), gathered per Omega_inc
+// cell over its own link records: the velocity at the wall point X is interpolated between the cell
+// and the cell behind the wall, the force (u_IB - u_X)/dt is spread to the cell with the fluid-side
+// weight of Eq. distribution_function, and a cell whose weights add up to more than 1 takes their
+// normalised sum.  All reads use the unforced u*, so the result does not depend on thread order.
 template <class T>
 __global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __restrict__ inc, long long n_inc,
                                                         const T* __restrict__ us, double* __restrict__ delta, T dt,
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __
         const long long X = inc[q];
         const unsigned fl = D.flags[X];
         T d3[3] = {0, 0, 0};
+        T wsum = 0;
         const bool dead = deadend_on && __popc(fl & 63u) >= 5;
         if (!dead) {
             for (int bit = 0; bit < 6; ++bit) {
@@ -144,28 +147,20 @@ __global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __
                 const LinkRec& r = link_record(D, X, fl, bit);
                 const long long G = r.far;
                 const T d = (T)r.d, wn = (T)r.w_near;
+                wsum += wn;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const T uX = ((T)1 - d) * us[c * D.N + X] + d * us[c * D.N + G];
                     const T Fc = ((T)r.uib[c] - uX) / dt;
                     d3[c] += dt * wn * Fc;
                 }
-                const unsigned flG = D.flags[G];
-                const int back = bit ^ 1;                  // the same link seen from G
-                const LinkRec& r2 = link_record(D, G, flG, back);
-                const T d2 = (T)r2.d, wf = (T)r2.w_far;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const T uX = ((T)1 - d2) * us[c * D.N + G] + d2 * us[c * D.N + X];
-                    const T Fc = ((T)r2.uib[c] - uX) / dt;
-                    d3[c] += dt * wf * Fc;
-                }
             }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            delta[3 * q + c] = (double)d3[c];
-            acc[c] += (double)d3[c] * vol;
+            const T dc = wsum > (T)1 ? d3[c] / wsum : d3[c];
+            delta[3 * q + c] = (double)dc;
+            acc[c] += (double)dc * vol;
         }
     }
     grid_reduce<3>(acc, partials, counter, [&](double* tot) {

@@ -266,7 +266,7 @@ int run_poisson(const LesCtx& c, PoissonWork& w, const double* b, double* x, dou
         out.outer = outer;
         if (h.nonfinite || !isfinite(h.res2)) { rc = IBM_E_NONFINITE; break; }
         if (h.bb == 0.0 || h.res2 <= tol * tol * h.bb) { rc = IBM_OK; break; }
-        if (h.iters >= maxit || outer >= max_outer) { rc = IBM_E_NOCONV; break; }
+        if (h.iters >= maxit || (solver != IBM_SOLVER_RBSOR && outer >= max_outer)) { rc = IBM_E_NOCONV; break; }
         ++outer;
         if (solver == IBM_SOLVER_RBSOR) {
             for (int it = 0; it < check_every; ++it) {

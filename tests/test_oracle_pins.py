@@ -485,20 +485,33 @@ def test_forcing_zero_at_wall_velocity_and_linear():
     o1, f1 = case.forcing(us)
     o2, f2 = case.forcing(2.5 * us)
     assert np.allclose(o2 - 2.5 * us, 2.5 * (o1 - us), atol=1e-12)
-    # one record pair: cell P (centre 4.5) sees the wall at d = 0.8, its far cell G = 5 at 0.2
+    # one wall between cells 4 (centre 4.5, wall at d = 0.8) and 5 (wall at d = 0.2): each cell is
+    # pulled towards u_IB = 0 by its own record with the fluid-side weight d/(1 + d) of the printed D
     u = np.zeros(3 * N)
     u[:N] = 1.0
     o, _ = case.forcing(u)
     x = np.arange(N) % 12
     d = float(np.float32(5.3)) - 4.5
-    wn, wf = d / (1 + d), (1 - d) / (1 + d)
-    # P gets its own near weight plus the far weight of G's record (G's d is 1 - d)
-    dG_own = (1 - d) / (1 + (1 - d))
-    dG_far = (1 - (1 - d)) / (1 + (1 - d))
-    expP = 1.0 + wn * (-1.0) + dG_far * (-1.0)
-    expG = 1.0 + dG_own * (-1.0) + wf * (-1.0)
+    expP = 1.0 - d / (1 + d)
+    expG = 1.0 - (1 - d) / (1 + (1 - d))
     assert np.allclose(o[:N][x == 4], expP) and np.allclose(o[:N][x == 5], expG)
     assert np.allclose(o[:N][(x != 4) & (x != 5)], 1.0)
+    # a cell crossed by several walls whose weights add up to more than 1 takes their normalised sum:
+    # cell (4, 4) boxed by walls at 4.05 and 4.95 in x and y (d = 0.45 on four links, total weight
+    # 4 * 0.45 / 1.45 > 1); with u* uniform every wall velocity interpolates to u*, so the normalised
+    # force lands the cell exactly on u_IB = 0 (the plain sum would overshoot to -0.24)
+    lo, hi = -40.0, 120.0
+    walls = [[[4.05, lo, lo], [4.05, hi, lo], [4.05, lo, hi]], [[4.95, lo, lo], [4.95, hi, lo], [4.95, lo, hi]],
+             [[lo, 4.05, lo], [lo, 4.05, hi], [hi, 4.05, lo]], [[lo, 4.95, lo], [lo, 4.95, hi], [hi, 4.95, lo]]]
+    box = oracle.Case(9, 9, 5, bc=SLIPBOX)
+    box.set_geometry(np.array(walls, np.float32))
+    P = 4 + 9 * (4 + 9 * 2)
+    assert bin(int(box.flags[P]) & 63).count("1") == 4
+    assert 4 * 0.45 / 1.45 > 1.0
+    u = np.zeros(3 * box.N)
+    u[:box.N] = 1.0
+    o, _ = box.forcing(u)
+    assert abs(o[P]) < 1e-6
 
 
 def test_deadend_filter_cancels_forcing():
