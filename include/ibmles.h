@@ -104,6 +104,22 @@ int ibm_classify(const ibm_grid* grid, const float* d_tri, int64_t ntri, const i
                  uint8_t* d_flags, int64_t* d_face_id, double* d_t_lo, double* d_t_hi, int64_t cap,
                  int64_t* n_cut, int64_t* n_tests, void* d_workspace, size_t ws_bytes, void* stream);
 
+/* ibm_classify without any device allocation, for callers that cannot call cudaMalloc -- for
+ * example code that runs under a host framework owning every device allocation through its own
+ * pool, or code that must not trigger the implicit device synchronisation an allocation can cause.
+ * The paper has no counterpart: this is a packaging variant of ibm_classify (same arguments and
+ * results, no d_workspace).  Its scratch is a fixed 32 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits; grids and soups whose
+ * ibm_classify_workspace_bytes() exceed it are rejected with IBM_E_INVALID before any device work.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (other streams or threads, same device) race and must be
+ * serialised by the caller.  Each call re-initialises what it needs, so earlier contents do not
+ * matter. */
+int ibm_classify_noalloc(const ibm_grid* grid, const float* d_tri, int64_t ntri, const ibm_geom_params* gp,
+                         uint8_t* d_flags, int64_t* d_face_id, double* d_t_lo, double* d_t_hi, int64_t cap,
+                         int64_t* n_cut, int64_t* n_tests, void* stream);
+
 /* Setup (Sec. 2.4.1 Eq. dummy_cell_region, Sec. 2.4.2 Eq. q_axis and Eq. distribution_function):
  * sets flags bits 6-7 in place and builds two link records per cut face (one per side) with the
  * ghost branch, its coefficients and the forcing weights.  The returned geometry owns its device

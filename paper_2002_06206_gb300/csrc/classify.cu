@@ -564,3 +564,53 @@ void ibm_geom_device(const ibm_geom* G, const uint8_t** flags, const int32_t** c
 }
 const ibm_grid* ibm_geom_grid(const ibm_geom* G) { return &G->grid; }
 int ibm_geom_deadend(const ibm_geom* G) { return G->gp.deadend_on ? 1 : 0; }
+
+// ------------------------------------------------------------------------------------------------
+// Classification without any allocation, for callers that cannot call cudaMalloc.
+//
+// The scratch lives in a fixed device array of this file.  Its name in host code is only a host-side
+// stand-in, so the device address is looked up once per device with cudaGetSymbolAddress (with that
+// device current) and cached; kernels receive that address.
+
+#include <mutex>
+
+#define IBM_NOALLOC_SCRATCH_BYTES (32u << 20)   // 32 MiB, held by every GPU that loads the library
+#define IBM_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[IBM_NOALLOC_SCRATCH_BYTES];
+
+static void* g_noalloc_ptr[IBM_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+extern "C" int ibm_classify_noalloc(const ibm_grid* g, const float* d_tri, int64_t ntri, const ibm_geom_params* gp,
+                                    uint8_t* d_flags, int64_t* d_face_id, double* d_t_lo, double* d_t_hi,
+                                    int64_t cap, int64_t* n_cut, int64_t* n_tests, void* stream) {
+    int rc = ibm_check_grid(g);
+    if (rc) return rc;
+    if (ntri < 0) return ibm_fail(IBM_E_INVALID, "ibm_classify_noalloc: negative triangle count");
+    const size_t need = ibm_classify_workspace_bytes(g, ntri);
+    if (need > IBM_NOALLOC_SCRATCH_BYTES)
+        return ibm_fail(IBM_E_INVALID,
+                        "ibm_classify_noalloc: this grid and soup need %zu bytes of scratch, more than the "
+                        "%u bytes the library reserves; use ibm_classify with a caller workspace",
+                        need, (unsigned)IBM_NOALLOC_SCRATCH_BYTES);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return ibm_cuda_check(e, "ibm_classify_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= IBM_NOALLOC_MAX_DEVICES)
+        return ibm_fail(IBM_E_INVALID, "ibm_classify_noalloc: device ordinal %d not supported", dev);
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return ibm_cuda_check(e, "ibm_classify_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // every part of the scratch that must start from a known value is initialised by ibm_classify
+    return ibm_classify(g, d_tri, ntri, gp, d_flags, d_face_id, d_t_lo, d_t_hi, cap, n_cut, n_tests, scratch,
+                        IBM_NOALLOC_SCRATCH_BYTES, stream);
+}
