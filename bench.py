@@ -45,6 +45,7 @@ def bytes_per_cell(s):
         "cg_dir_spmv": 4 * s + 1,         # r, p_old, flags -> p, q
         "cg_update": 6 * s,               # x, p, r, q -> x, r
         "correct": 12 * s + 9,            # u*, U*, p (fp64), flags -> u, U
+        "mg_fine": 2 * s + 1,             # one red-black colour pass: z (all), r and z (one colour), flags
     }
 
 
@@ -219,6 +220,124 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------------------------
 
+def time_classify(L, torch, name="vehicle_1024x512x384", repeats=5):
+    """ibm_classify on the vehicle-like assembly (separate from the step): median of `repeats` runs,
+    in predicate tests per second; the soup and buffers are resident on the device."""
+    import ctypes as C
+    cfg = W.get_config(name)
+    tri = torch.from_numpy(cfg.soup()).cuda()
+    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
+    lib = L.lib()
+    N = cfg.ncell
+    ws = torch.empty(lib.ibm_classify_workspace_bytes(C.byref(g), tri.shape[0]), dtype=torch.uint8, device="cuda")
+    flags = torch.empty(N, dtype=torch.uint8, device="cuda")
+    cap = 4 * tri.shape[0] + 1024
+    fid = torch.empty(cap, dtype=torch.int64, device="cuda")
+    tlo = torch.empty(cap, dtype=torch.float64, device="cuda")
+    thi = torch.empty(cap, dtype=torch.float64, device="cuda")
+    gp = L.GeomParams(1e-9, 0.0, cfg.deadend_on, 0)
+    stream = torch.cuda.current_stream()
+    times, ncut, ntests = [], C.c_int64(), C.c_int64()
+    for _ in range(repeats + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = lib.ibm_classify(C.byref(g), C.c_void_p(tri.data_ptr()), tri.shape[0], C.byref(gp),
+                              C.c_void_p(flags.data_ptr()), C.c_void_p(fid.data_ptr()), C.c_void_p(tlo.data_ptr()),
+                              C.c_void_p(thi.data_ptr()), cap, C.byref(ncut), C.byref(ntests),
+                              C.c_void_p(ws.data_ptr()), ws.numel(), C.c_void_p(stream.cuda_stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            return {"workload": name, "error": lib.ibm_last_error().decode()}
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times[1:]))
+    return {"workload": name, "triangles": int(tri.shape[0]), "cells": N, "ms": ms,
+            "predicate_tests": int(ntests.value), "mtests_per_s": ntests.value / (ms * 1e-3) / 1e6,
+            "links_per_s": 3 * N / (ms * 1e-3), "cut_faces": int(ncut.value),
+            "note": "median of %d after one warm-up; includes the per-face table fill, compaction and the "
+                    "host read of the cut count" % repeats}
+
+
+def net_init(seed=0, scale=0.05):
+    """Initial parameters of the guess network (layout of include/ibmles.h)."""
+    rng = np.random.default_rng(seed)
+    w = [rng.standard_normal(8 * 27 * 8), rng.standard_normal(8 * 27 * 8), rng.standard_normal(27 * 8)]
+    return np.concatenate([x * scale for x in w] + [np.zeros(17)]).astype(np.float32)
+
+
+def timed_steps(torch, solver, st, steps, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    stats = []
+    e0.record(stream)
+    for _ in range(steps):
+        stats.append(solver.step(st).as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), stats
+
+
+def run_learned(args, L, torch, solver, st, geo, cfg, world):
+    """Learned initial guess: snapshots (b, p^n, p^{n-1}, p^{n+1}) from the solver's own steps, Adam
+    training on the GPU with the library's kernels, then K steps without and K steps with the guess
+    from the same point of the run."""
+    N = cfg.ncell
+    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
+    stream = torch.cuda.current_stream()
+    snaps = []
+    p_prev = st["p"].clone()
+    t0 = time.time()
+    for n in range(args.learn_snapshots + 2):
+        p_n = st["p"].clone()
+        solver.step(st)
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        solver.last_rhs(b)
+        if n >= 2:
+            snaps.append((b, p_n, p_prev, st["p"].clone()))
+        p_prev = p_n
+    torch.cuda.synchronize()
+    t_collect = time.time() - t0
+    net = L.Net(net_init())
+    t0 = time.time()
+    losses = []
+    for epoch in range(args.learn_epochs):
+        for (b, p_n, p_p, p_next) in snaps:
+            _, sc = net.forward(g, b, p_n, p_p, geo.flags)
+            target = ((p_next - p_n) / sc).to(torch.float32)
+            losses.append(net.train_step(g, b, p_n, p_p, target, args.learn_lr, geo.flags))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del snaps
+    torch.cuda.empty_cache()
+    ms_plain, st_plain = timed_steps(torch, solver, st, args.steps, stream)
+    solver.attach_guess(net)
+    solver.step(st)                       # the guess needs p^{n-1}
+    ms_learn, st_learn = timed_steps(torch, solver, st, args.steps, stream)
+    solver.attach_guess(None)
+    ms_plain = max_over_ranks(ms_plain, world)
+    ms_learn = max_over_ranks(ms_learn, world)
+    ratios = [s["relres_guess"] / s["relres0"] for s in st_learn if s["relres0"] > 0]
+    net.close()
+    return {
+        "value": N * args.steps * world / (ms_learn * 1e-3) / 1e6,
+        "ms_per_step": ms_learn / args.steps,
+        "plain_same_window": {"value": N * args.steps * world / (ms_plain * 1e-3) / 1e6,
+                              "ms_per_step": ms_plain / args.steps,
+                              "inner_iters_per_step": float(np.mean([s["iters"] for s in st_plain])),
+                              "refinements_per_step": float(np.mean([s["outer"] for s in st_plain]))},
+        "inner_iters_per_step": float(np.mean([s["iters"] for s in st_learn])),
+        "refinements_per_step": float(np.mean([s["outer"] for s in st_learn])),
+        "guess_used_fraction": float(np.mean([s["guess_used"] for s in st_learn])),
+        "median_initial_residual_ratio": float(np.median(ratios)) if ratios else None,
+        "max_relres": float(max(s["relres"] for s in st_learn)),
+        "train": {"snapshots": args.learn_snapshots, "epochs": args.learn_epochs, "lr": args.learn_lr,
+                  "loss_first": losses[0], "loss_last": losses[-1], "collect_s": t_collect, "train_s": t_train},
+        "note": "plain and learned windows are consecutive, after the training snapshots; same solver state",
+    }
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -234,9 +353,10 @@ def run_ours(args):
     tri = cfg.soup()
     g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
     geo = L.Geometry(g, torch.from_numpy(tri).cuda(), deadend_on=cfg.deadend_on)
+    precond = L.MULTIGRID if args.precond == "mg" else L.NO_PRECOND
     solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=cfg.precision, solver=L.CG, tol=cfg.tol,
                       max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
-                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo)
+                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond)
     st = solver.fields(W.initial_fields(cfg))
     for _ in range(args.warmup):
         solver.step(st)
@@ -247,9 +367,10 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(local)
 
-    # ---- timed region: K steps, inputs resident in HBM, per-kernel events on the launching stream
+    # ---- timed region: K steps, inputs resident in HBM, the library's fast path (CUDA graphs on)
     iters, outers, relres = [], [], []
-    solver.profile(1)
+    solver.profile(0)
+    n_launch0 = solver.kernel_launches()
     barrier(world)
     torch.cuda.synchronize()
     with Clocks(gpu_id) as clk:
@@ -262,12 +383,20 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    prof = solver.profile_read()
-    launches = solver.kernel_launches()
-    solver.profile(0)
+    launches = solver.kernel_launches() - n_launch0
     barrier(world)
     ms_max = max_over_ranks(ms, world)
     clocks = clk.summary()
+
+    # ---- the same number of steps again with per-kernel CUDA events on the launching stream (the
+    # profiler records around every kernel group, so graphs are not used here): kernel durations
+    solver.profile(1)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        solver.step(st)
+    torch.cuda.synchronize()
+    prof = solver.profile_read()
+    solver.profile(0)
 
     # ---- end to end through the public API with host buffers: H2D of the step's inputs from pinned
     # memory, the step, D2H of its result, every step
@@ -301,12 +430,16 @@ def run_ours(args):
     s_bytes = 8 if cfg.precision == L.FP64 else 4
     bpc = bytes_per_cell(s_bytes)
     timed = {k: v for k, v in prof.items() if v[1] > 0 and k in bpc}
+    everything = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(timed, key=lambda k: timed[k][0])
     avg_ms = timed[dom][0] / timed[dom][1]
     algo_bytes = bpc[dom] * N
     peak, peak_kind = read_peaks()
     achieved = algo_bytes / (avg_ms * 1e-3) / 1e9
-    shares = {k: round(v[0] / sum(x[0] for x in timed.values()), 4) for k, v in timed.items()}
+    shares = {k: round(v[0] / sum(x[0] for x in everything.values()), 4) for k, v in everything.items()}
+
+    learned = run_learned(args, L, torch, solver, st, geo, cfg, world) if args.learned else None
+    classify = None if args.no_classify else time_classify(L, torch)
 
     line = None
     if rank == 0:
@@ -318,14 +451,16 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "cells": N, "grid": [cfg.nx, cfg.ny, cfg.nz],
                        "triangles": int(len(tri)), "precision": "fp32 stencils and cg, fp64 residual refinement",
-                       "solver": "cg", "tol": cfg.tol, "parallelism": "replicas" if world > 1 else "single",
+                       "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.4 GB of state per step vs 126 MB L2)",
                        "inner_iters_per_step": I, "refinements_per_step": float(np.mean(outers)),
                        "max_relres": float(np.max(relres))},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": ncu_traffic(dom),
                          "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ms,
-                         "peak_source": peak_kind, "shares": shares},
+                         "peak_source": peak_kind, "shares": shares,
+                         "note": "kernel times from a second pass of the same number of steps with per-kernel "
+                                 "events (graphs off); shares are of event-timed kernel time"},
             "cpu_baseline": None if cpu is None else {
                 "value": N / cpu["t_step_s"] / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": cpu["sample"]},
@@ -333,6 +468,8 @@ def run_ours(args):
                     "steps": ke},
             "gpu_launches": launches,
             "clocks": clocks,
+            "classify": classify,
+            "learned": learned,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -348,10 +485,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--precond", default="mg", choices=["mg", "none"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-classify", action="store_true")
+    ap.add_argument("--learned", action="store_true", help="also time the learned initial guess")
+    ap.add_argument("--learn-snapshots", type=int, default=24)
+    ap.add_argument("--learn-epochs", type=int, default=8)
+    ap.add_argument("--learn-lr", type=float, default=2e-3)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -69,20 +69,27 @@ typedef struct {
     int32_t check_every; /* iterations between host reads of the residual (0 = 16) */
     double inner_tol;    /* FP32 inner solve: relative reduction per FP64 refinement (0 = 1e-4) */
     double sor_omega;    /* over-relaxation factor of red-black SOR (0 = 1.9) */
+    int32_t precond;     /* CG preconditioner: 0 none, 1 geometric multigrid V-cycle */
+    int32_t mg_sweeps;   /* red-black Gauss-Seidel sweeps before and after each coarse correction (0 = 2) */
+    double mg_omega;     /* multigrid coarse-correction factor in (0, 2) (0 = 1.6) */
+    double quick;        /* fraction of QUICK in the advected face value, [0, 1] (Sec. 3.1/3.3: 0.05-0.1) */
 } les_params;
 
 typedef struct {
     int32_t iters;       /* inner iterations of the last pressure solve */
     int32_t outer;       /* FP64 refinement passes of the last pressure solve */
     int32_t status;      /* ibm_status of the solve */
-    int32_t reserved;
+    int32_t guess_used;  /* 1 if the solve started from the learned guess */
     double relres;       /* ||b - A p|| / ||b|| at exit, computed in FP64 */
     double bnorm;        /* ||b||_2 */
     double fsum[3];      /* momentum added by the IB forcing this step: sum of du * dx^3 */
+    double relres0;      /* with a learned guess attached: initial ||b - A p^n|| / ||b|| (else -1) */
+    double relres_guess; /* with a learned guess attached: initial residual of the guess (else -1) */
 } les_stats;
 
 typedef struct ibm_geom ibm_geom;
 typedef struct les_state les_state;
+typedef struct ibm_net ibm_net;
 
 /* ---------------------------------------------------------------------------------------------- */
 /* Geometry: classification (Sec. 2.4.1: ray tracing from the cell centres along the grid lines,    */
@@ -187,12 +194,45 @@ int forces(les_state* st, const float* d_tri, int64_t ntri, const double* d_p, d
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around each kernel group of
  * les_step / poisson_solve.  les_profile(st, 1) enables and resets the counters, (st, 0) disables.
- * les_profile_read (synchronises) fills ms[10] (total milliseconds) and launches[10] per group, in
- * the order: csm, predict, forcing, faces, rhs, residual, cg_dir_spmv, cg_update, correct, sor. */
+ * les_profile_read (synchronises) fills ms[13] (total milliseconds) and launches[13] per group, in
+ * the order: csm, predict, forcing, faces, rhs, residual, cg_dir_spmv, cg_update, correct, sor,
+ * mg_fine (fine-grid smoothing passes), mg_transfer (fine-grid restriction and prolongation),
+ * mg_coarse (everything on the coarse levels, one group per V-cycle). */
 int les_profile(les_state* st, int32_t on);
 int les_profile_read(les_state* st, double* ms, int64_t* launches);
 /* Kernels this state launched since les_create or the last les_profile(st, 1) (host counter). */
 int64_t les_kernel_launches(const les_state* st);
+
+/* ---------------------------------------------------------------------------------------------- */
+/* Learned initial guess of the pressure solve.  Not in the paper: a small 3-D convolutional network  */
+/* (3x3x3 kernels, 8 -> 8 -> 8 -> 1 channels, ReLU) that maps, per cell, the right-hand side b dx^2,  */
+/* the last pressure change p^n - p^{n-1} (both divided by s = RMS of p^n - p^{n-1}) and the solid    */
+/* mask (cells with a cut link) to (p^{n+1} - p^n) / s.  BF16 weights and activations, FP32         */
+/* accumulation on the tensor cores.  Parameters: W1[8][27][8], W2[8][27][8], W3[1][27][8], b1[8],    */
+/* b2[8], b3[1] (ibm_net_num_params() floats), tap = 9 (dz+1) + 3 (dy+1) + (dx+1).                    */
+
+int ibm_net_num_params(void);
+/* h_params (host, may be NULL for zeros): initial parameters. */
+int ibm_net_create(const float* h_params, ibm_net** out);
+void ibm_net_destroy(ibm_net* net);
+int ibm_net_get_params(const ibm_net* net, float* h_params);
+/* Gradients of the last ibm_net_train_step (mean squared error), same layout as the parameters. */
+int ibm_net_get_grads(const ibm_net* net, float* h_grads);
+/* d_out[N] (float) = network output for the snapshot (b, p, p_prev, flags); *scale (host, may be NULL,
+ * synchronises) = s.  d_flags may be NULL (no body). */
+int ibm_net_forward(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
+                    const double* d_pprev, const uint8_t* d_flags, float* d_out, double* scale, void* stream);
+/* One Adam step (betas 0.9, 0.999) on the mean squared error against d_target[N] = (p^{n+1} - p^n)/s;
+ * lr = 0 only computes the gradients.  *loss (host, synchronises) = the loss before the update. */
+int ibm_net_train_step(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
+                       const double* d_pprev, const uint8_t* d_flags, const float* d_target, float lr,
+                       double* loss, void* stream);
+/* Attach (or detach with NULL) a network to a solver state: from the second step on, each les_step
+ * starts the pressure solve from p^n + s net(...) when that iterate has the smaller residual, else from
+ * p^n.  The state keeps p^{n-1}.  The network must stay alive while attached. */
+int les_attach_guess(les_state* st, ibm_net* net);
+/* Copy the right-hand side b of the last les_step / les_rhs into d_b[N]. */
+int les_last_rhs(les_state* st, double* d_b, void* stream);
 
 /* Number of faces NF of the concatenated face vector for this grid (-1 for an invalid grid). */
 int64_t les_num_faces(const ibm_grid* grid);

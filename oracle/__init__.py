@@ -35,7 +35,7 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("u_in", C.c_double * 3),
                 ("bc", C.c_int32 * 6), ("csm_on", C.c_int32), ("forcing_on", C.c_int32),
-                ("deadend_on", C.c_int32), ("pad_", C.c_int32)]
+                ("deadend_on", C.c_int32), ("pad_", C.c_int32), ("quick", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -114,13 +114,13 @@ class Case:
     """Grid + physics parameters + (optionally) a classified geometry, all held by the oracle."""
 
     def __init__(self, nx, ny, nz, dx=1.0, nu=0.0, dt=1.0, bc=(0, 0, 0, 0, 0, 0),
-                 u_in=(1.0, 0.0, 0.0), csm_on=1, forcing_on=1, deadend_on=0):
+                 u_in=(1.0, 0.0, 0.0), csm_on=1, forcing_on=1, deadend_on=0, quick=0.0):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
         self.NF = nfaces(nx, ny, nz)
         self.g = Grid(nx, ny, nz, 0, dx)
         self.pr = Params(nu, dt, (C.c_double * 3)(*u_in), (C.c_int32 * 6)(*bc), csm_on,
-                         forcing_on, deadend_on, 0)
+                         forcing_on, deadend_on, 0, quick)
         self.flags = np.zeros(self.N, np.uint8)
         self.rec = np.zeros(0, RECORD_DTYPE)
         self.cellrec = np.full(self.N, -1, np.int64)
@@ -130,7 +130,7 @@ class Case:
     @classmethod
     def from_config(cls, cfg):
         return cls(cfg.nx, cfg.ny, cfg.nz, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
-                   cfg.forcing_on, cfg.deadend_on)
+                   cfg.forcing_on, cfg.deadend_on, cfg.quick)
 
     # -- geometry ------------------------------------------------------------------------------
     def classify(self, tri, eps_edge=1e-9, eps_det=0.0):

@@ -438,6 +438,31 @@ static double face_velocity(const or_grid* g, const double* U, int64_t P, int a,
     return U[face_at(g, a, x)];
 }
 
+/* Advected value on the face of P towards side s along axis a (Sec. 3.1/3.3: central differencing
+ * blended with a fraction `quick` of QUICK, the "hybrid" scheme).  With L the lower and R the upper
+ * cell of the face, QUICK takes (6 upwind + 3 downwind - far upwind)/8, the far upwind value read
+ * across the upwind cell's outer link (neighbour, ghost or boundary value).  Both cells of a face get
+ * the same value, so the advective fluxes still telescope. */
+static double face_advected(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                            const int64_t* cellrec, const double* u, int comp, int64_t P, int a, int s,
+                            double uP, double uN, double Uf) {
+    const int64_t N = ncells(g);
+    double central = 0.5 * (uP + uN);
+    if (pr->quick == 0.0) return central;
+    int64_t Nb;
+    if (is_cut(flags, P, a, s) || !neighbour(g, pr, P, a, s, &Nb)) return central;
+    int64_t Lc = s > 0 ? P : Nb, Rc = s > 0 ? Nb : P;
+    double uL = u[comp * N + Lc], uR = u[comp * N + Rc], q;
+    if (Uf >= 0.0) {
+        double far = or_velocity_across(g, pr, flags, rec, cellrec, u, comp, Lc, a, -1);
+        q = (6.0 * uL + 3.0 * uR - far) / 8.0;
+    } else {
+        double far = or_velocity_across(g, pr, flags, rec, cellrec, u, comp, Rc, a, +1);
+        q = (6.0 * uR + 3.0 * uL - far) / 8.0;
+    }
+    return (1.0 - pr->quick) * central + pr->quick * q;
+}
+
 void or_predict(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 const int64_t* cellrec, const double* u, const double* U, const double* nut,
                 const double* Hprev, double* H, double* ustar, int first_step) {
@@ -463,7 +488,7 @@ void or_predict(const or_grid* g, const or_params* pr, const uint8_t* flags, con
                     if (i == a) T = D1;
                     else if (interior) T = (double)s * 0.5 * (GP[i][a] + GN[i][a]);
                     else T = (double)s * GP[i][a];
-                    double conv = -(double)s * Uf * 0.5 * (uP + uN);
+                    double conv = -(double)s * Uf * face_advected(g, pr, flags, rec, cellrec, u, i, P, a, s, uP, uN, Uf);
                     h[i] += conv + (nu + nutf) * D1 + nutf * T;
                 }
             }

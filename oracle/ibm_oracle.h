@@ -33,6 +33,7 @@ typedef struct {
     int32_t forcing_on;   /* distributed forcing on (Eq. discrete_forcing_term) */
     int32_t deadend_on;   /* dead-end filter B (Eq. deadend_filter) */
     int32_t pad_;
+    double quick;         /* weight of the QUICK face value in the advective flux (hybrid scheme), 0..1 */
 } or_params;
 
 /* One link record: the cut link of cell `cell` in direction side*e_axis (Sec. 2.4.1, Eq. q_axis). */

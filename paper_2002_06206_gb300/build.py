@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibmles.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = {"classify.cu": ["-fmad=false"], "les.cu": [], "poisson.cu": [], "api.cu": []}
+SOURCES = {"classify.cu": ["-fmad=false"], "les.cu": [], "poisson.cu": [], "mg.cu": [], "stencil4.cu": [], "learn.cu": [], "api.cu": []}
 
 
 def nvcc():

@@ -3,6 +3,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <math.h>
 #include <string.h>
 
 #include "solver.cuh"
@@ -82,6 +83,12 @@ struct les_state {
     double* hfs;        // pinned: forcing sums of the last step
     size_t s;           // bytes of a field value
     long long nlaunch;  // kernel launches since creation or the last les_profile(st, 1)
+    ibm_net* net;       // learned initial guess, or null
+    double* p_prev;     // p^{n-1}
+    double* p_keep;     // p^n kept across the solve
+    double* x_guess;
+    double* two_res;    // [2] residual norms of p^n and of the guess
+    long long steps;    // steps taken (the guess needs p^{n-1})
 };
 
 static void free_state(les_state* S) {
@@ -99,14 +106,33 @@ static void free_state(les_state* S) {
     cudaFree(S->w.rh);
     cudaFree(S->w.sv);
     cudaFree(S->w.tv);
+    cudaFree(S->w.vb);
     cudaFree(S->w.sc);
     cudaFreeHost(S->w.hsc);
     cudaFreeHost(S->hfs);
     if (S->w.ev) cudaEventDestroy(S->w.ev);
+    if (S->w.gexec) cudaGraphExecDestroy(S->w.gexec);
+    if (S->w.cap) cudaStreamDestroy(S->w.cap);
     cudaFree(S->c.partials);
     cudaFree(S->c.counter);
     cudaFree(S->c.fscal);
     cudaFree(S->c.fdelta);
+    cudaFree(S->w.z);
+    cudaFree(S->p_prev);
+    cudaFree(S->p_keep);
+    cudaFree(S->x_guess);
+    cudaFree(S->two_res);
+    if (S->c.mg) {
+        for (int l = 1; l < S->c.mg->nlev; ++l) {
+            MGLev& L = S->c.mg->lev[l];
+            for (int a = 0; a < 3; ++a) cudaFree(L.g[a]);
+            cudaFree(L.d);
+            cudaFree(L.invdg);
+            cudaFree(L.b);
+            cudaFree(L.x);
+        }
+        free(S->c.mg);
+    }
     prof_free(S->c.prof);
     free(S);
 }
@@ -127,6 +153,11 @@ static int check_params(const les_params* p) {
             return ibm_fail(IBM_E_INVALID, "periodic boundary on axis %d must be set on both faces", a);
     if (!(p->dt > 0.0) || !(p->nu >= 0.0)) return ibm_fail(IBM_E_INVALID, "dt must be > 0 and nu >= 0");
     if (!(p->tol > 0.0)) return ibm_fail(IBM_E_INVALID, "tol must be > 0");
+    if (p->precond != 0 && p->precond != 1) return ibm_fail(IBM_E_INVALID, "unknown preconditioner %d", p->precond);
+    if (p->precond && p->mg_omega != 0.0 && !(p->mg_omega > 0.0 && p->mg_omega < 2.0))
+        return ibm_fail(IBM_E_INVALID, "mg_omega must lie in (0, 2) for a symmetric positive preconditioner");
+    if (p->precond && p->mg_sweeps < 0) return ibm_fail(IBM_E_INVALID, "mg_sweeps must be >= 0");
+    if (!(p->quick >= 0.0 && p->quick <= 1.0)) return ibm_fail(IBM_E_INVALID, "quick must lie in [0, 1]");
     return IBM_OK;
 }
 
@@ -170,9 +201,13 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     c.F = make_faces(g->nx, g->ny, g->nz);
     c.NF = c.F.off[2] + (long long)c.F.dim[2][0] * c.F.dim[2][1] * c.F.dim[2][2];
     c.cg = cell_grid(g->nx, g->ny, g->nz);
+    c.fgrid = flat_grid(g->nx, g->ny, g->nz);
+    c.pgrid = flat_grid(g->nx, g->ny, g->nz, 1);
+    c.cgrid = flat_grid(g->nx, g->ny, g->nz, 2 * IBM_KU);
     c.prec = p->precision;
     c.nu = p->nu;
     c.dt = p->dt;
+    c.quick = p->quick;
     c.csm_on = p->csm_on;
     c.forcing_on = p->forcing_on;
     c.deadend_on = geom ? ibm_geom_deadend(geom) : 0;
@@ -188,8 +223,16 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     ALLOC(S->w.pb, N * s);
     ALLOC(S->w.q, N * s);
     if (p->precision != IBM_FP64) ALLOC(S->w.e, N * 4);
+    if (p->solver == IBM_SOLVER_BICGSTAB) {
+        ALLOC(S->w.rh, N * s);
+        ALLOC(S->w.sv, N * s);
+        ALLOC(S->w.tv, N * s);
+        ALLOC(S->w.vb, N * s);
+    }
     ALLOC(S->w.sc, sizeof(SolveScal));
     size_t nblk = cell_blocks(c.cg);
+    const size_t nflat = (size_t)c.fgrid.x * c.fgrid.y * c.fgrid.z;   // >= the 4-cell launches' blocks
+    if (nblk < nflat) nblk = nflat;
     if (nblk < 32 * IBM_NSM) nblk = 32 * IBM_NSM;
     ALLOC(c.partials, nblk * 8 * sizeof(double));
     ALLOC(c.counter, 16 * sizeof(unsigned));
@@ -208,12 +251,72 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     }
     memset(S->hfs, 0, 8 * sizeof(double));
     S->c.nlaunch = &S->nlaunch;
+    if (p->precond == 1) {
+        MG* mg = (MG*)calloc(1, sizeof(MG));
+        if (!mg) {
+            free_state(S);
+            return ibm_fail(IBM_E_NOMEM, "les_create: host allocation");
+        }
+        S->c.mg = mg;
+        mg->sweeps = p->mg_sweeps > 0 ? p->mg_sweeps : 2;
+        mg->omega = p->mg_omega > 0.0 ? p->mg_omega : 1.6;
+        mg->coarse_sweeps = 8;
+        int dims[IBM_MG_MAXLEV][3];
+        mg->nlev = mg_levels_for(g->nx, g->ny, g->nz, dims, IBM_MG_MAXLEV);
+        for (int l = 0; l < mg->nlev; ++l) {
+            MGLev& L = mg->lev[l];
+            L.nx = dims[l][0];
+            L.ny = dims[l][1];
+            L.nz = dims[l][2];
+            L.sy = L.nx;
+            L.sz = (long long)L.nx * L.ny;
+            L.N = L.sz * L.nz;
+            for (int a = 0; a < 3; ++a) L.per[a] = p->bc[2 * a] == IBM_BC_PERIODIC;
+            if (l == 0) continue;
+            for (int a = 0; a < 3; ++a) ALLOC(L.g[a], (size_t)L.N * sizeof(float));
+            ALLOC(L.d, (size_t)L.N * sizeof(float));
+            ALLOC(L.invdg, (size_t)L.N * sizeof(float));
+            ALLOC(L.b, (size_t)L.N * s);
+            ALLOC(L.x, (size_t)L.N * s);
+        }
+        ALLOC(S->w.z, N * s);
+        if ((e = cudaStreamCreateWithFlags(&S->w.cap, cudaStreamNonBlocking)) != cudaSuccess) {
+            free_state(S);
+            return ibm_cuda_check(e, "les_create: capture stream");
+        }
+        int rc2 = mg_setup(S->c, *mg, 0);
+        if (!rc2 && (e = cudaDeviceSynchronize()) != cudaSuccess) rc2 = ibm_cuda_check(e, "les_create: multigrid set-up");
+        if (rc2) {
+            free_state(S);
+            return rc2;
+        }
+    }
     *out = S;
     return IBM_OK;
 }
 
 #define NEED(x) \
     if (!(x)) return ibm_fail(IBM_E_INVALID, "%s: null argument (%s)", __func__, #x)
+
+extern "C" int les_attach_guess(les_state* S, ibm_net* net) {
+    NEED(S);
+    if (net && !S->p_prev) {
+        const size_t N = (size_t)S->c.D.N;
+        cudaError_t e;
+        if ((e = cudaMalloc(&S->p_prev, N * 8)) != cudaSuccess || (e = cudaMalloc(&S->p_keep, N * 8)) != cudaSuccess ||
+            (e = cudaMalloc(&S->x_guess, N * 8)) != cudaSuccess || (e = cudaMalloc(&S->two_res, 2 * 8)) != cudaSuccess)
+            return ibm_fail(IBM_E_NOMEM, "les_attach_guess: %s", cudaGetErrorString(e));
+        S->steps = 0;
+    }
+    S->net = net;
+    return IBM_OK;
+}
+
+extern "C" int les_last_rhs(les_state* S, double* d_b, void* stream) {
+    NEED(S); NEED(d_b);
+    IBM_CUDA(cudaMemcpyAsync(d_b, S->b, (size_t)S->c.D.N * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return IBM_OK;
+}
 
 extern "C" int les_init_faces(les_state* S, const void* u, void* U, void* stream) {
     NEED(S); NEED(u); NEED(U);
@@ -329,7 +432,8 @@ extern "C" int poisson_solve(les_state* S, const double* b, double* p, double to
     NEED(S); NEED(b); NEED(p);
     if (!(tol > 0.0) || max_it < 0 || solver < IBM_SOLVER_CG || solver > IBM_SOLVER_RBSOR)
         return ibm_fail(IBM_E_INVALID, "poisson_solve: bad tol/max_it/solver");
-    if (solver == IBM_SOLVER_BICGSTAB) return ibm_fail(IBM_E_INVALID, "poisson_solve: BiCGStab is not built yet");
+    if (solver == IBM_SOLVER_BICGSTAB && !S->w.rh)
+        return ibm_fail(IBM_E_INVALID, "poisson_solve: BiCGStab needs a state created with solver = IBM_SOLVER_BICGSTAB");
     int rc = run_poisson(S->c, S->w, b, p, tol, max_it, solver, S->prm.check_every, S->prm.inner_tol,
                          S->prm.sor_omega, st, (cudaStream_t)stream);
     if (rc == IBM_E_NOCONV) ibm_fail(rc, "poisson_solve: no convergence within %d iterations", max_it);
@@ -364,16 +468,43 @@ extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int3
     prof_begin(c.prof, PS_RHS, s);
     if ((rc = launch_rhs(c, S->Ustar, S->b, s))) return rc;
     prof_end(c.prof, PS_RHS, s);
-    const int solver = S->prm.solver == IBM_SOLVER_BICGSTAB ? IBM_SOLVER_CG : S->prm.solver;
+    const int solver = S->prm.solver;
     les_stats ps = {};
+    int guess_used = 0;
+    double r0 = -1.0, rg = -1.0;
+    if (S->net) {
+        // learned initial guess: start from it only if its residual is below that of p^n
+        const size_t nb = (size_t)c.D.N * 8;
+        IBM_CUDA(cudaMemcpyAsync(S->p_keep, p, nb, cudaMemcpyDeviceToDevice, s));
+        if (S->steps >= 1) {
+            if ((rc = net_guess(S->net, &S->grid, S->b, p, S->p_prev, c.D.flags, S->x_guess, s))) return rc;
+            if ((rc = launch_two_residuals(c, S->b, p, S->x_guess, S->two_res, s))) return rc;
+            double h[2];
+            IBM_CUDA(cudaMemcpyAsync(h, S->two_res, sizeof(h), cudaMemcpyDeviceToHost, s));
+            IBM_CUDA(cudaStreamSynchronize(s));
+            r0 = h[0];
+            rg = h[1];
+            if (h[1] < h[0]) {
+                IBM_CUDA(cudaMemcpyAsync(p, S->x_guess, nb, cudaMemcpyDeviceToDevice, s));
+                guess_used = 1;
+            }
+        }
+    }
     int prc = run_poisson(c, S->w, S->b, p, S->prm.tol, S->prm.max_iter > 0 ? S->prm.max_iter : 100000, solver,
                           S->prm.check_every, S->prm.inner_tol, S->prm.sor_omega, &ps, s);
     if (prc != IBM_OK && prc != IBM_E_NOCONV) return prc;
     prof_begin(c.prof, PS_CORRECT, s);
     if ((rc = launch_correct(c, S->ustar, S->Ustar, p, u, U, s))) return rc;
     prof_end(c.prof, PS_CORRECT, s);
+    if (S->net) {
+        IBM_CUDA(cudaMemcpyAsync(S->p_prev, S->p_keep, (size_t)c.D.N * 8, cudaMemcpyDeviceToDevice, s));
+        S->steps += 1;
+    }
     if (st) {
         *st = ps;
+        st->guess_used = guess_used;
+        st->relres0 = (r0 >= 0.0 && ps.bnorm > 0.0) ? sqrt(r0) / ps.bnorm : -1.0;
+        st->relres_guess = (rg >= 0.0 && ps.bnorm > 0.0) ? sqrt(rg) / ps.bnorm : -1.0;
         for (int q = 0; q < 3; ++q) st->fsum[q] = forcing ? S->hfs[q] : 0.0;
     }
     if (prc == IBM_E_NOCONV) return ibm_fail(prc, "les_step: pressure solve did not converge");

@@ -166,30 +166,75 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], double* __restrict_
     }
 }
 
+// Flat launch of the stencil kernels: 32 x 8 threads over an (x, y) tile, each thread handling
+// IBM_KU consecutive planes (loop fully unrolled, so all its loads are independent and in flight
+// together).
+#define IBM_KU 4
+inline dim3 flat_grid(int nx, int ny, int nz, int planes = IBM_KU) {
+    return dim3((unsigned)((nx + IBM_TX - 1) / IBM_TX), (unsigned)((ny + IBM_TY - 1) / IBM_TY),
+                (unsigned)((nz + planes - 1) / planes));
+}
+
+// 7-point link sum  sum_links g (v_N - v_P) - d v_P  of a value function on the fine grid, with a
+// fast path for a cell with no cut link away from the domain faces (g = 1 on all six links).
+template <class T, class Get>
+__device__ __forceinline__ T link_sum7(const Dom& D, long long P, int i, int j, int k, unsigned fl, T vP, Get get) {
+    if (fl == 0u && i > 0 && i < D.nx - 1 && j > 0 && j < D.ny - 1 && k > 0 && k < D.nz - 1)
+        return ((get(P - 1) + get(P + 1)) + (get(P - D.sy) + get(P + D.sy))) + (get(P - D.sz) + get(P + D.sz)) -
+               (T)6 * vP;
+    const int x[3] = {i, j, k};
+    T sum = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            const int bit = 2 * a + (s > 0);
+            if (fl & (1u << bit)) continue;
+            long long off;
+            if (nb_offset(D, a, s, x[a], off)) sum += get(P + off) - vP;
+            else if (D.bc[bit] == IBM_BC_OUTFLOW) sum += -vP - vP;
+        }
+    return sum;
+}
+
 // Launch geometry of the cell kernels.
 struct CellGrid {
     dim3 grid, block;
     int kchunk;
 };
 
-inline CellGrid cell_grid(int nx, int ny, int nz) {
+// Chooses the z-chunk so that the blocks fill whole waves of the SMs: with `res` resident blocks of
+// 256 threads per SM, a launch takes ceil(blocks / (res * SMs)) waves of (kchunk + 1) plane steps
+// (the +1 is the plane each column loads before its first one).
+inline CellGrid cell_grid(int nx, int ny, int nz, int res = 4) {
     CellGrid g;
     g.block = dim3(IBM_TX, IBM_TY, 1);
-    int gx = (nx + IBM_TX - 1) / IBM_TX, gy = (ny + IBM_TY - 1) / IBM_TY;
-    long long want = 8LL * IBM_NSM;       // ~8 resident blocks of 256 threads per SM
-    long long gz = (want + (long long)gx * gy - 1) / ((long long)gx * gy);
-    if (gz < 1) gz = 1;
-    if (gz > nz) gz = nz;
-    g.kchunk = (int)((nz + gz - 1) / gz);
-    gz = (nz + g.kchunk - 1) / g.kchunk;
-    g.grid = dim3(gx, gy, (unsigned)gz);
+    const long long gx = (nx + IBM_TX - 1) / IBM_TX, gy = (ny + IBM_TY - 1) / IBM_TY;
+    const long long slots = (long long)res * IBM_NSM;
+    long long best_cost = -1;
+    int best_k = nz;
+    for (int gz = 1; gz <= nz; ++gz) {
+        const int kc = (nz + gz - 1) / gz;
+        const long long gze = (nz + kc - 1) / kc;
+        const long long blocks = gx * gy * gze;
+        const long long waves = (blocks + slots - 1) / slots;
+        const long long cost = waves * (kc + 1);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_k = kc;
+        }
+        if (kc == 1) break;
+    }
+    g.kchunk = best_k;
+    g.grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)((nz + best_k - 1) / best_k));
     return g;
 }
 
 inline unsigned cell_blocks(const CellGrid& g) { return g.grid.x * g.grid.y * g.grid.z; }
 
-// Host-side error recording (api.cu).
+// Host-side error recording and argument checks (api.cu).
 int ibm_fail(int code, const char* fmt, ...);
+int ibm_check_grid(const ibm_grid* g);
 int ibm_cuda_check(cudaError_t e, const char* what);
 #define IBM_CUDA(call)                                                     \
     do {                                                                   \

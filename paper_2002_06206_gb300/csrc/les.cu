@@ -24,56 +24,145 @@ __device__ __forceinline__ void grad_at(const Dom& D, const T* __restrict__ u, l
 
 __device__ __forceinline__ unsigned flags_at(const Dom& D, long long P) { return D.flags ? (unsigned)D.flags[P] : 0u; }
 
-// Eq. Smagorinsky with the coherent-structure coefficient of Eq. Q / Eq. FCS.
+// Eq. Smagorinsky with the coherent-structure coefficient of Eq. Q / Eq. FCS.  One thread per cell.
 template <class T>
-__global__ void __launch_bounds__(256) k_csm(Dom D, const T* __restrict__ u, T* __restrict__ nut, int kchunk) {
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+__global__ void __launch_bounds__(256) k_csm(Dom D, const T* __restrict__ u, T* __restrict__ nut) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
     const T inv2dx = (T)(0.5 / D.dx), delta2 = (T)(D.dx * D.dx);
-    for (int k = k0; k < k1; ++k) {
-        const long long P = i + (long long)D.sy * j + D.sz * k;
-        const unsigned fl = flags_at(D, P);
-        const int x[3] = {i, j, k};
-        T G[3][3];
-        grad_at(D, u, P, x, fl, inv2dx, G);
-        T SS = 0, WW = 0;
+    const long long P = i + (long long)D.sy * j + D.sz * k;
+    const unsigned fl = flags_at(D, P);
+    const int x[3] = {i, j, k};
+    T G[3][3];
+    if (fl == 0u && i > 0 && i < D.nx - 1 && j > 0 && j < D.ny - 1 && k > 0 && k < D.nz - 1) {
+        const long long o[3] = {1, (long long)D.sy, D.sz};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const T S = (T)0.5 * (G[a][b] + G[b][a]);
-                const T W = (T)0.5 * (G[a][b] - G[b][a]);
-                SS += S * S;
-                WW += W * W;
-            }
-        const T Q = (T)0.5 * (WW - SS), E = (T)0.5 * (WW + SS);
-        const T F = E > (T)0 ? Q / E : (T)0;
-        const T aF = F < (T)0 ? -F : F;
-        const T C = (T)(1.0 / 20.0) * (aF * sqrt(aF));
-        nut[P] = C * delta2 * sqrt(SS);
+            for (int b = 0; b < 3; ++b) G[a][b] = (u[b * D.N + P + o[a]] - u[b * D.N + P - o[a]]) * inv2dx;
+    } else {
+        grad_at(D, u, P, x, fl, inv2dx, G);
     }
+    T SS = 0, WW = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const T S = (T)0.5 * (G[a][b] + G[b][a]);
+            const T W = (T)0.5 * (G[a][b] - G[b][a]);
+            SS += S * S;
+            WW += W * W;
+        }
+    const T Q = (T)0.5 * (WW - SS), E = (T)0.5 * (WW + SS);
+    const T F = E > (T)0 ? Q / E : (T)0;
+    const T aF = F < (T)0 ? -F : F;
+    const T C = (T)(1.0 / 20.0) * (aF * sqrt(aF));
+    nut[P] = C * delta2 * sqrt(SS);
+}
+
+// Advected value on the face of P towards side s along axis a: the central value blended with a
+// fraction gam of QUICK (6 upwind + 3 downwind - far upwind)/8, the far upwind value read across the
+// upwind cell's outer link.  L and R are the lower and upper cells of the face, so both cells of a face
+// compute the same value.  Cut faces and domain faces keep the central value.
+template <class T>
+__device__ __forceinline__ T face_adv(const Dom& D, const T* __restrict__ u, int c, long long P, const int x[3],
+                                      unsigned fl, int a, int s, T uP, T uN, T Uf, T gam) {
+    const T central = (T)0.5 * (uP + uN);
+    if (gam == (T)0) return central;
+    long long off;
+    if ((fl & (1u << (2 * a + (s > 0)))) || !nb_offset(D, a, s, x[a], off)) return central;
+    const int n = a == 0 ? D.nx : (a == 1 ? D.ny : D.nz);
+    const long long Nn = P + off;
+    const long long Lc = s > 0 ? P : Nn, Rc = s > 0 ? Nn : P;
+    const int xo = x[a] + s < 0 ? n - 1 : (x[a] + s >= n ? 0 : x[a] + s);
+    const int xL = s > 0 ? x[a] : xo, xR = s > 0 ? xo : x[a];
+    const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
+    T q;
+    if (Uf >= (T)0) {
+        const T far = vel_across(D, u, c, Lc, xL, D.flags ? (unsigned)D.flags[Lc] : 0u, a, -1);
+        q = ((T)6 * uL + (T)3 * uR - far) / (T)8;
+    } else {
+        const T far = vel_across(D, u, c, Rc, xR, D.flags ? (unsigned)D.flags[Rc] : 0u, a, +1);
+        q = ((T)6 * uR + (T)3 * uL - far) / (T)8;
+    }
+    return ((T)1 - gam) * central + gam * q;
 }
 
 // Momentum predictor: flux-form central advection with the face velocity U, diffusion with
-// nu + nu_t, the transpose part of the SGS stress divergence, Adams-Bashforth 2 in time.
+// nu + nu_t, the transpose part of the SGS stress divergence, Adams-Bashforth 2 in time.  One thread
+// per cell; a cell whose six neighbours and itself have no cut link and which lies off the domain
+// faces reads every value directly (the same formulas as the general path, which goes through the
+// ghost and boundary rules of vel_across).
 template <class T>
 __global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
                                                  const T* __restrict__ nut, const T* Hprev, T* H,
-                                                 T* __restrict__ ustar, T nu, T dt, int first, int kchunk) {
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+                                                 T* __restrict__ ustar, T nu, T dt, int first, T gam) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
     const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
     const int n[3] = {D.nx, D.ny, D.nz};
-    for (int k = k0; k < k1; ++k) {
-        const long long P = i + (long long)D.sy * j + D.sz * k;
-        const unsigned fl = flags_at(D, P);
-        const int x[3] = {i, j, k};
+    const long long P = i + (long long)D.sy * j + D.sz * k;
+    const unsigned fl = flags_at(D, P);
+    const int x[3] = {i, j, k};
+    const long long o[3] = {1, (long long)D.sy, D.sz};
+    const int mrg = gam != (T)0 ? 2 : 1;    // QUICK reads two cells away
+    bool fast = fl == 0u && i >= mrg && i < D.nx - mrg && j >= mrg && j < D.ny - mrg && k >= mrg && k < D.nz - mrg;
+    if (fast && D.flags) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fast = fast && D.flags[P - o[a]] == 0 && D.flags[P + o[a]] == 0;
+    }
+    const T nutP = nut[P];
+    T h[3] = {0, 0, 0};
+    if (fast) {
+        T uc[3], un[3][6], GP[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            uc[c] = u[c * D.N + P];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                un[c][2 * a] = u[c * D.N + P - o[a]];
+                un[c][2 * a + 1] = u[c * D.N + P + o[a]];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int s = -1; s <= 1; s += 2) {
+                const int lb = 2 * a + (s > 0);
+                const T Uf = U[F.index(a, x[0] + (a == 0 && s > 0), x[1] + (a == 1 && s > 0), x[2] + (a == 2 && s > 0))];
+                const long long Nn = P + s * o[a];
+                const T nutf = (T)0.5 * (nutP + nut[Nn]);
+                T GN[3] = {0, 0, 0};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (q == a) continue;
+                    GN[q] = (u[a * D.N + Nn + o[q]] - u[a * D.N + Nn - o[q]]) * inv2dx;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T uP = uc[c], uN = un[c][lb];
+                    const T D1 = (uN - uP) * invdx;
+                    const T Tt = c == a ? D1 : (T)s * (T)0.5 * (GP[c][a] + GN[c]);
+                    T adv = (T)0.5 * (uP + uN);
+                    if (gam != (T)0) {
+                        // L = P (s > 0) or P - e_a (s < 0); far upwind is L - e_a or R + e_a
+                        const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
+                        const long long Lc = s > 0 ? P : Nn, Rc = s > 0 ? Nn : P;
+                        const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - u[c * D.N + Lc - o[a]]) / (T)8
+                                               : ((T)6 * uR + (T)3 * uL - u[c * D.N + Rc + o[a]]) / (T)8;
+                        adv = ((T)1 - gam) * adv + gam * q;
+                    }
+                    const T conv = -(T)s * Uf * adv;
+                    h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
+                }
+            }
+    } else {
         T GP[3][3];
         grad_at(D, u, P, x, fl, inv2dx, GP);
-        const T nutP = nut[P];
-        T h[3] = {0, 0, 0};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -108,19 +197,19 @@ __global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* _
                     if (c == a) Tt = D1;
                     else if (interior) Tt = (T)s * (T)0.5 * (GP[c][a] + GN[c]);
                     else Tt = (T)s * GP[c][a];
-                    const T conv = -(T)s * Uf * (T)0.5 * (uP + uN);
+                    const T conv = -(T)s * Uf * face_adv(D, u, c, P, x, fl, a, s, uP, uN, Uf, gam);
                     h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
                 }
             }
+    }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long long o = c * D.N + P;
-            const T hc = h[c] * invdx;
-            const T uP = u[o];
-            const T hp = first ? (T)0 : Hprev[o];
-            H[o] = hc;
-            ustar[o] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
-        }
+    for (int c = 0; c < 3; ++c) {
+        const long long oc = c * D.N + P;
+        const T hc = h[c] * invdx;
+        const T uP = u[oc];
+        const T hp = first ? (T)0 : Hprev[oc];
+        H[oc] = hc;
+        ustar[oc] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
     }
 }
 
@@ -287,33 +376,32 @@ __global__ void k_outflow_shift(Dom D, FaceLayout F, T* __restrict__ Us, const d
     }
 }
 
-// Eq. poisson right-hand side: b = div(U*) / dt, evaluated in FP64.
+// Eq. poisson right-hand side: b = div(U*) / dt, evaluated in the working precision and stored in
+// FP64 (the pressure solve's FP64 residual b - A p starts from it).
 template <class T>
 __global__ void __launch_bounds__(256) k_rhs(Dom D, FaceLayout F, const T* __restrict__ Us, double* __restrict__ b,
-                                             double inv_dxdt, int kchunk) {
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+                                             double inv_dxdt) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
-    const double dxdt = 1.0 / inv_dxdt;
-    for (int k = k0; k < k1; ++k) {
+    const T inv = (T)inv_dxdt;
+    {
         const long long P = i + (long long)D.sy * j + D.sz * k;
-        double div = 0.0;
-        div += (double)Us[F.index(0, i + 1, j, k)] - (double)Us[F.index(0, i, j, k)];
-        div += (double)Us[F.index(1, i, j + 1, k)] - (double)Us[F.index(1, i, j, k)];
-        div += (double)Us[F.index(2, i, j, k + 1)] - (double)Us[F.index(2, i, j, k)];
-        b[P] = div / dxdt;
+        T div = 0;
+        div += Us[F.index(0, i + 1, j, k)] - Us[F.index(0, i, j, k)];
+        div += Us[F.index(1, i, j + 1, k)] - Us[F.index(1, i, j, k)];
+        div += Us[F.index(2, i, j, k + 1)] - Us[F.index(2, i, j, k)];
+        b[P] = (double)(div * inv);
     }
 }
 
 // Eq. correction on the cells: central pressure gradient through the link values.
 template <class T>
 __global__ void __launch_bounds__(256) k_correct_cells(Dom D, const T* __restrict__ us, const double* __restrict__ p,
-                                                       T* __restrict__ u, double dt, int kchunk) {
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
+                                                       T* __restrict__ u, double dt) {
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
-    const double twodx = 2.0 * D.dx;
-    for (int k = k0; k < k1; ++k) {
+    const T c = (T)(dt / (2.0 * D.dx));     // the FP64 pressure difference is rounded once, then scaled
+    {
         const long long P = i + (long long)D.sy * j + D.sz * k;
         const unsigned fl = flags_at(D, P);
         const int x[3] = {i, j, k};
@@ -321,7 +409,7 @@ __global__ void __launch_bounds__(256) k_correct_cells(Dom D, const T* __restric
         for (int a = 0; a < 3; ++a) {
             const double pp = p_across(D, p, P, x[a], fl, a, +1);
             const double pm = p_across(D, p, P, x[a], fl, a, -1);
-            u[a * D.N + P] = (T)((double)us[a * D.N + P] - dt * (pp - pm) / twodx);
+            u[a * D.N + P] = us[a * D.N + P] - c * (T)(pp - pm);
         }
     }
 }
@@ -362,7 +450,7 @@ __global__ void k_correct_faces(Dom D, FaceLayout F, int a, const T* __restrict_
                 continue;
             }
         }
-        U[fi] = (T)((double)Us[fi] - dt * (pr - pl) / D.dx);
+        U[fi] = Us[fi] - (T)(dt / D.dx) * (T)(pr - pl);
     }
 }
 
@@ -435,9 +523,9 @@ unsigned lin_blocks(long long n, int threads) {
 
 int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
     if (c.prec == IBM_FP64)
-        k_csm<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, (const double*)u, (double*)nut, c.cg.kchunk);
+        k_csm<double><<<c.pgrid, c.cg.block, 0, s>>>(c.D, (const double*)u, (double*)nut);
     else
-        k_csm<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, (const float*)u, (float*)nut, c.cg.kchunk);
+        k_csm<float><<<c.pgrid, c.cg.block, 0, s>>>(c.D, (const float*)u, (float*)nut);
     IBM_LAUNCHED("k_csm");
     IBM_COUNT(c, 1);
     return IBM_OK;
@@ -446,14 +534,14 @@ int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
 int launch_predict(const LesCtx& c, const void* u, const void* U, const void* nut, const void* Hprev, void* H,
                    void* ustar, int first, cudaStream_t s) {
     if (c.prec == IBM_FP64)
-        k_predict<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)u, (const double*)U,
-                                                           (const double*)nut, (const double*)Hprev, (double*)H,
-                                                           (double*)ustar, c.nu, c.dt, first, c.cg.kchunk);
+        k_predict<double><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)u, (const double*)U,
+                                                         (const double*)nut, (const double*)Hprev, (double*)H,
+                                                         (double*)ustar, c.nu, c.dt, first, c.quick);
     else
-        k_predict<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)u, (const float*)U,
-                                                          (const float*)nut, (const float*)Hprev, (float*)H,
-                                                          (float*)ustar, (float)c.nu, (float)c.dt, first,
-                                                          c.cg.kchunk);
+        k_predict<float><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)u, (const float*)U,
+                                                        (const float*)nut, (const float*)Hprev, (float*)H,
+                                                        (float*)ustar, (float)c.nu, (float)c.dt, first,
+                                                        (float)c.quick);
     IBM_LAUNCHED("k_predict");
     IBM_COUNT(c, 1);
     return IBM_OK;
@@ -501,9 +589,9 @@ int launch_faces(const LesCtx& c, const void* ustar, void* Ustar, cudaStream_t s
 int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s) {
     const double inv = 1.0 / (c.D.dx * c.dt);
     if (c.prec == IBM_FP64)
-        k_rhs<double><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)Ustar, b, inv, c.cg.kchunk);
+        k_rhs<double><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)Ustar, b, inv);
     else
-        k_rhs<float><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)Ustar, b, inv, c.cg.kchunk);
+        k_rhs<float><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)Ustar, b, inv);
     IBM_LAUNCHED("k_rhs");
     IBM_COUNT(c, 1);
     return IBM_OK;
@@ -511,7 +599,7 @@ int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s) {
 
 template <class T>
 static void correct_t(const LesCtx& c, const T* us, const T* Us, const double* p, T* u, T* U, cudaStream_t s) {
-    k_correct_cells<T><<<c.cg.grid, c.cg.block, 0, s>>>(c.D, us, p, u, c.dt, c.cg.kchunk);
+    k_correct_cells<T><<<c.pgrid, c.cg.block, 0, s>>>(c.D, us, p, u, c.dt);
     for (int a = 0; a < 3; ++a) {
         const long long nf = (long long)c.F.dim[a][0] * c.F.dim[a][1] * c.F.dim[a][2];
         k_correct_faces<T><<<lin_blocks(nf, 256), 256, 0, s>>>(c.D, c.F, a, Us, p, U, c.dt);

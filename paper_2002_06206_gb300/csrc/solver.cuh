@@ -8,6 +8,7 @@ struct SolveScal {
     double bb, res2, rr32;              // ||b||^2, ||b - A x||^2 in FP64, ||r||^2 of the FP32 copy
     double rho, rho_old, alpha, omega;  // BiCGStab
     double ts, tt, ss, rv;              // BiCGStab inner products
+    double rz, rz_old;                  // preconditioned CG: (r, z) and its previous value
     int done, iters, restart, nonfinite;
     int maxit, pad0, pad1, pad2;
 };
@@ -15,7 +16,7 @@ struct SolveScal {
 // Optional per-kernel timing with CUDA events on the launching stream (les_profile).
 enum ProfSlot {
     PS_CSM = 0, PS_PREDICT, PS_FORCING, PS_FACES, PS_RHS, PS_RESIDUAL, PS_CG_SPMV, PS_CG_UPDATE, PS_CORRECT,
-    PS_SOR, PS_COUNT
+    PS_SOR, PS_MG_FINE, PS_MG_TRANSFER, PS_MG_COARSE, PS_COUNT
 };
 struct Prof {
     int on;
@@ -28,12 +29,37 @@ struct Prof {
 void prof_begin(Prof* p, int slot, cudaStream_t s);
 void prof_end(Prof* p, int slot, cudaStream_t s);
 
+// One level of the multigrid preconditioner (mg.cu).  Level 0 is the fine grid and keeps its links in
+// the flags; coarser levels store the conductance of each cell's +x, +y, +z link.
+#define IBM_MG_MAXLEV 12
+struct MGLev {
+    int nx, ny, nz;
+    long long N, sy, sz;
+    int per[3];          // periodic axes
+    float* g[3];         // conductance of the +a link
+    float* d;            // Dirichlet (outflow) diagonal term
+    float* invdg;        // 1 / (sum of link conductances + d), 0 for an isolated cell
+    void* b;             // right-hand side (working precision)
+    void* x;             // iterate (working precision)
+};
+struct MG {
+    int nlev;
+    int sweeps;          // red-black passes before and after the coarse correction, per level
+    int coarse_sweeps;   // symmetric sweeps on the coarsest level
+    double omega;        // coarse-correction factor, 0 < omega < 2
+    MGLev lev[IBM_MG_MAXLEV];
+};
+
 struct LesCtx {
     Dom D;
     FaceLayout F;
     CellGrid cg;
+    dim3 fgrid;               // flat launch (IBM_KU planes per thread)
+    dim3 pgrid;               // flat launch, one cell per thread
+    dim3 cgrid;               // flat launch over same-colour cell pairs (2 * IBM_KU planes per thread)
     int prec;                 // IBM_FP64 / IBM_FP32_REFINE64
     double nu, dt;
+    double quick;             // QUICK fraction of the advected face value (hybrid scheme)
     int csm_on, forcing_on, deadend_on;
     const int32_t* inc;       // Omega_inc cells
     long long n_inc, n_rec;
@@ -44,6 +70,7 @@ struct LesCtx {
     double* fdelta;           // [3 * n_inc] forcing increments
     Prof* prof;               // null unless profiling
     long long* nlaunch;       // running count of kernel launches (host memory)
+    MG* mg;                   // multigrid preconditioner, null for plain CG
 };
 
 #define IBM_COUNT(c, n) \
@@ -62,7 +89,20 @@ int launch_forces(const LesCtx& c, const float* tri, long long ntri, const doubl
                   cudaStream_t s);
 
 // poisson.cu
+// stencil4.cu: FP32 fine-grid kernels with 4 cells per thread (nx a multiple of 4)
+bool x4_ok(const LesCtx& c);
+void launch_cg_dir_spmv_x4(const LesCtx& c, const float* src, const float* pold, float* pnew, float* q, float idx2,
+                           SolveScal* sc, int pcg, cudaStream_t s);
+void launch_mg_smooth0_x4(const LesCtx& c, const float* r, float* z, float scale, int col, int zero, int fin,
+                          SolveScal* sc, cudaStream_t s);
+
+int mg_levels_for(int nx, int ny, int nz, int dims[][3], int maxlev);
+int mg_setup(const LesCtx& c, MG& mg, cudaStream_t s);
+template <class T>
+int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cudaStream_t s);
+
 struct PoissonWork {
+    void* z;        // preconditioned residual (MG-PCG)
     void* r;        // Krylov vectors of the working precision
     void* pa;
     void* pb;
@@ -71,10 +111,23 @@ struct PoissonWork {
     void* rh;       // BiCGStab shadow residual
     void* sv;       // BiCGStab s
     void* tv;       // BiCGStab t
+    void* vb;       // BiCGStab second v buffer (v is read at the neighbours while the next is written)
     SolveScal* sc;  // device scalars
     SolveScal* hsc; // pinned host copy
     cudaEvent_t ev;
+    // CUDA graph of two preconditioned iterations (both ping-pong parities), replayed while the
+    // per-kernel profiler is off; captured on `cap` for the solution vector `gkey` in precision `gprec`
+    cudaStream_t cap;
+    cudaGraphExec_t gexec;
+    const void* gkey;
+    int gprec;
+    long long glaunches;
 };
 int launch_apply64(const LesCtx& c, const double* p, double* Ap, cudaStream_t s);
+int launch_two_residuals(const LesCtx& c, const double* b, const double* xa, const double* xb, double* out,
+                         cudaStream_t s);
+// learn.cu
+int net_guess(ibm_net* n, const ibm_grid* g, const double* b, const double* p, const double* pprev,
+              const uint8_t* flags, double* xg, cudaStream_t s);
 int run_poisson(const LesCtx& c, PoissonWork& w, const double* b, double* x, double tol, int maxit, int solver,
                 int check_every, double inner_tol, double omega, les_stats* st, cudaStream_t s);

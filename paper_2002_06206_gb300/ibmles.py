@@ -17,6 +17,7 @@ OK, E_INVALID, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_CAPACITY = range(7)
 PERIODIC, INFLOW, OUTFLOW, SLIP, NOSLIP = range(5)
 FP64, FP32_REFINE64 = 0, 1
 CG, BICGSTAB, RBSOR = 0, 1, 2
+NO_PRECOND, MULTIGRID = 0, 1
 
 
 class IbmError(RuntimeError):
@@ -39,16 +40,20 @@ class Params(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("u_in", C.c_double * 3), ("bc", C.c_int32 * 6),
                 ("csm_on", C.c_int32), ("forcing_on", C.c_int32), ("precision", C.c_int32),
                 ("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("check_every", C.c_int32), ("inner_tol", C.c_double), ("sor_omega", C.c_double)]
+                ("check_every", C.c_int32), ("inner_tol", C.c_double), ("sor_omega", C.c_double),
+                ("precond", C.c_int32), ("mg_sweeps", C.c_int32), ("mg_omega", C.c_double),
+                ("quick", C.c_double)]
 
 
 class Stats(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("status", C.c_int32), ("reserved", C.c_int32),
-                ("relres", C.c_double), ("bnorm", C.c_double), ("fsum", C.c_double * 3)]
+    _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("status", C.c_int32), ("guess_used", C.c_int32),
+                ("relres", C.c_double), ("bnorm", C.c_double), ("fsum", C.c_double * 3),
+                ("relres0", C.c_double), ("relres_guess", C.c_double)]
 
     def as_dict(self):
         return {"iters": self.iters, "outer": self.outer, "status": self.status, "relres": self.relres,
-                "bnorm": self.bnorm, "fsum": list(self.fsum)}
+                "bnorm": self.bnorm, "fsum": list(self.fsum), "guess_used": self.guess_used,
+                "relres0": self.relres0, "relres_guess": self.relres_guess}
 
 
 _lib = None
@@ -87,6 +92,17 @@ SIGNATURES = {
     "les_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "les_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "les_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "ibm_net_num_params": (C.c_int, []),
+    "ibm_net_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ibm_net_destroy": (None, [C.c_void_p]),
+    "ibm_net_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ibm_net_get_grads": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ibm_net_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ibm_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_float, C.c_void_p, C.c_void_p]),
+    "les_attach_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "les_last_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ibm_last_error": (C.c_char_p, []),
 }
 
@@ -213,13 +229,14 @@ class Solver:
 
     def __init__(self, grid, nu, dt, bc, u_in=(1.0, 0.0, 0.0), precision=FP64, solver=CG, tol=1e-6,
                  max_iter=100000, check_every=16, inner_tol=1e-4, sor_omega=1.9, csm_on=1, forcing_on=1,
-                 geometry=None):
+                 geometry=None, precond=NO_PRECOND, mg_sweeps=2, mg_omega=1.6, quick=0.0):
         self.grid = grid
         self.N = grid.nx * grid.ny * grid.nz
         self.NF = num_faces(grid.nx, grid.ny, grid.nz)
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.params = Params(nu, dt, (C.c_double * 3)(*u_in), (C.c_int32 * 6)(*bc), csm_on, forcing_on,
-                             precision, solver, tol, max_iter, check_every, inner_tol, sor_omega)
+                             precision, solver, tol, max_iter, check_every, inner_tol, sor_omega, precond,
+                             mg_sweeps, mg_omega, quick)
         self.geometry = geometry
         h = C.c_void_p()
         _check(lib().les_create(C.byref(grid), C.byref(self.params),
@@ -292,23 +309,86 @@ class Solver:
         return list(out)
 
     PROFILE_SLOTS = ("csm", "predict", "forcing", "faces", "rhs", "residual", "cg_dir_spmv", "cg_update",
-                     "correct", "sor")
+                     "correct", "sor", "mg_fine", "mg_transfer", "mg_coarse")
 
     def profile(self, on):
         _check(lib().les_profile(self.handle, int(on)))
 
     def profile_read(self):
-        ms = (C.c_double * 10)()
-        n = (C.c_int64 * 10)()
+        ms = (C.c_double * 13)()
+        n = (C.c_int64 * 13)()
         _check(lib().les_profile_read(self.handle, ms, n))
         return {k: (ms[q], n[q]) for q, k in enumerate(self.PROFILE_SLOTS)}
 
     def kernel_launches(self):
         return int(lib().les_kernel_launches(self.handle))
 
+    def attach_guess(self, net):
+        _check(lib().les_attach_guess(self.handle, net.handle if net is not None else None))
+        self.net = net
+
+    def last_rhs(self, b, stream=None):
+        _check(lib().les_last_rhs(self.handle, _ptr(b, torch.float64), _stream(stream)))
+
     def close(self):
         if getattr(self, "handle", None):
             lib().les_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """Learned initial guess of the pressure solve (ibm_net_*): creation, forward, training steps."""
+
+    def __init__(self, params=None):
+        import numpy as np
+        self.n_params = int(lib().ibm_net_num_params())
+        h = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            assert arr.size == self.n_params
+            h = arr.ctypes.data_as(C.c_void_p)
+        handle = C.c_void_p()
+        _check(lib().ibm_net_create(h, C.byref(handle)))
+        self.handle = handle
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().ibm_net_get_params(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def grads(self):
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().ibm_net_get_grads(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def forward(self, grid, b, p, pprev, flags=None, stream=None):
+        N = grid.nx * grid.ny * grid.nz
+        out = torch.empty(N, dtype=torch.float32, device=b.device)
+        s = C.c_double()
+        _check(lib().ibm_net_forward(self.handle, C.byref(grid), _ptr(b, torch.float64), _ptr(p, torch.float64),
+                                     _ptr(pprev, torch.float64), _ptr(flags, torch.uint8) if flags is not None else None,
+                                     _ptr(out, torch.float32), C.byref(s), _stream(stream)))
+        return out, s.value
+
+    def train_step(self, grid, b, p, pprev, target, lr, flags=None, stream=None):
+        loss = C.c_double()
+        _check(lib().ibm_net_train_step(self.handle, C.byref(grid), _ptr(b, torch.float64), _ptr(p, torch.float64),
+                                        _ptr(pprev, torch.float64),
+                                        _ptr(flags, torch.uint8) if flags is not None else None,
+                                        _ptr(target, torch.float32), C.c_float(lr), C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ibm_net_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -43,17 +43,22 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     g = L.make_grid(0, 4, 4)
     out = C.c_void_p()
     prm = L.Params(0.1, 0.1, (C.c_double * 3)(1, 0, 0), (C.c_int32 * 6)(1, 2, 3, 3, 3, 3), 1, 1, 0, 0,
-                   1e-6, 100, 16, 1e-4, 1.9)
+                   1e-6, 100, 16, 1e-4, 1.9, 0, 2, 1.6, 0.0)
     assert lib.les_create(C.byref(g), C.byref(prm), None, C.byref(out)) == L.E_INVALID
     assert b"extent" in lib.ibm_last_error()
     g = L.make_grid(8, 8, 8)
     bad = L.Params(0.1, 0.1, (C.c_double * 3)(1, 0, 0), (C.c_int32 * 6)(0, 2, 3, 3, 3, 3), 1, 1, 0, 0,
-                   1e-6, 100, 16, 1e-4, 1.9)
+                   1e-6, 100, 16, 1e-4, 1.9, 0, 2, 1.6, 0.0)
     assert lib.les_create(C.byref(g), C.byref(bad), None, C.byref(out)) == L.E_INVALID
     assert b"periodic" in lib.ibm_last_error()
     bad.bc[0] = 1
     bad.precision = 7
     assert lib.les_create(C.byref(g), C.byref(bad), None, C.byref(out)) == L.E_INVALID
+    bad.precision = 0
+    bad.precond = 1
+    bad.mg_omega = 2.5
+    assert lib.les_create(C.byref(g), C.byref(bad), None, C.byref(out)) == L.E_INVALID
+    assert b"omega" in lib.ibm_last_error()
     big = L.make_grid(2048, 2048, 2048)
     assert lib.les_create(C.byref(big), C.byref(prm), None, C.byref(out)) == L.E_INVALID
     gp = L.GeomParams(1e-9, 0.0, 0, 0)

@@ -1,0 +1,156 @@
+"""Learned initial guess of the pressure solve: the tensor-core network kernels against the FP64 numpy
+reference, training on solver snapshots, and what the trained guess gains over starting from p^n.
+
+BF16 storage of weights and activations bounds the agreement: outputs to a relative L2 of 2e-2,
+gradients to 6e-2 (FP32 accumulation throughout)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import learned as NL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2002_06206_gb300 import build
+    build.build()
+    from paper_2002_06206_gb300 import ibmles
+    ibmles.lib()
+    return ibmles
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def flat_params(Wl, Bl):
+    return np.concatenate([Wl[0].ravel(), Wl[1].ravel(), Wl[2].ravel(), Bl[0], Bl[1], Bl[2]]).astype(np.float32)
+
+
+def unflat(v):
+    n1 = 8 * 27 * 8
+    W1 = v[:n1].reshape(8, 27, 8)
+    W2 = v[n1:2 * n1].reshape(8, 27, 8)
+    W3 = v[2 * n1:2 * n1 + 216].reshape(1, 27, 8)
+    o = 2 * n1 + 216
+    return [W1, W2, W3], [v[o:o + 8], v[o + 8:o + 16], v[o + 16:o + 17]]
+
+
+def features(b, p, pp, flags, dx, shape):
+    d = p - pp
+    s = np.sqrt(np.mean(d ** 2))
+    if s == 0:
+        s = np.sqrt(np.mean((b * dx * dx) ** 2)) or 1.0
+    x = np.zeros(shape + (8,))
+    x[..., 0] = (b * dx * dx / s).reshape(shape)
+    x[..., 1] = (d / s).reshape(shape)
+    x[..., 2] = ((flags & 63) != 0).reshape(shape)
+    return x, s
+
+
+def bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def _snapshot(shape, seed):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    b = rng.standard_normal(N)
+    p = rng.standard_normal(N)
+    pp = p + 0.3 * rng.standard_normal(N)
+    flags = (rng.random(N) < 0.1).astype(np.uint8) * 3
+    return b, p, pp, flags
+
+
+@pytest.mark.parametrize("shape", [(11, 13, 37), (8, 16, 32)])
+def test_network_forward_and_gradients_match_reference(L, shape):
+    nz, ny, nx = shape
+    g = L.make_grid(nx, ny, nz, 0.5)
+    b, p, pp, flags = _snapshot(shape, 3)
+    Wl, Bl = NL.init_params(seed=4, scale=0.15)
+    rng = np.random.default_rng(5)
+    Bl = [rng.standard_normal(8) * 0.05, rng.standard_normal(8) * 0.05, rng.standard_normal(1) * 0.05]
+    params = flat_params(Wl, Bl)
+    net = L.Net(params)
+    assert np.array_equal(net.params(), params)
+    t = lambda a, dt=torch.float64: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    out, s = net.forward(g, t(b), t(p), t(pp), t(flags, torch.uint8))
+    x, s_ref = features(b, p, pp, flags, 0.5, shape)
+    assert s == pytest.approx(s_ref, rel=1e-5)
+    Wb = [bf16(w) for w in Wl]
+    ref_out, _ = NL.forward(bf16(x), Wb, Bl)
+    assert rel(out.cpu().numpy(), ref_out[..., 0]) <= 2e-2
+    # gradients of the mean squared error (lr = 0: no update)
+    target = np.random.default_rng(6).standard_normal(shape)
+    loss = net.train_step(g, t(b), t(p), t(pp), t(target.ravel(), torch.float32), 0.0, t(flags, torch.uint8))
+    ref_loss, dW, dB, _ = NL.loss_and_grads(bf16(x), target, Wb, Bl)
+    assert loss == pytest.approx(ref_loss, rel=2e-2)
+    gW, gB = unflat(net.grads().astype(np.float64))
+    for l in range(3):
+        assert rel(gW[l], dW[l]) <= 6e-2, l
+        assert rel(gB[l], dB[l]) <= 6e-2, l
+    net.close()
+
+
+def test_training_lowers_the_loss(L):
+    shape = (16, 16, 32)
+    nz, ny, nx = shape
+    g = L.make_grid(nx, ny, nz)
+    b, p, pp, flags = _snapshot(shape, 7)
+    # a target the network can represent: a smoothed copy of the last pressure change
+    d = (p - pp).reshape(shape)
+    target = (d + np.roll(d, 1, 2) + np.roll(d, -1, 2)) / 3.0
+    x, s = features(b, p, pp, flags, 1.0, shape)
+    t = lambda a, dt=torch.float64: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    net = L.Net(flat_params(*NL.init_params(seed=1, scale=0.05)))
+    tgt = t((target / s).ravel(), torch.float32)
+    losses = [net.train_step(g, t(b), t(p), t(pp), tgt, 3e-3, t(flags, torch.uint8)) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], losses[::10]
+    net.close()
+
+
+def test_trained_guess_lowers_the_initial_residual(L):
+    """Train on snapshots of the first steps of a dirty-sphere run, then check on later steps that the
+    guess starts the pressure solve from a smaller residual than p^n and that the solve still converges."""
+    nx, ny, nz = 96, 48, 48
+    tri = W.dirty_sphere(seed=2, radius=6.0, center=(24.0, 24.0, 24.0), subdiv=4)
+    bc = (1, 2, 3, 3, 3, 3)
+    g = L.make_grid(nx, ny, nz)
+    geo = L.Geometry(g, torch.from_numpy(tri).cuda())
+    solver = L.Solver(g, 12.0 / 1e4, 0.2, bc, precision=L.FP32_REFINE64, tol=1e-6, geometry=geo, precond=L.MULTIGRID)
+    st = solver.fields(W.initial_fields(W.Config("d", nx, ny, nz, 0, 0, 0, 0, 0, bc, seed=2)))
+    N = nx * ny * nz
+    snaps = []
+    p_prev = st["p"].clone()
+    for n in range(40):
+        p_n = st["p"].clone()
+        solver.step(st)
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        solver.last_rhs(b)
+        if n >= 2:
+            snaps.append((b, p_n, p_prev, st["p"].clone()))
+        p_prev = p_n
+    net = L.Net(flat_params(*NL.init_params(seed=0, scale=0.05)))
+    for epoch in range(6):
+        for (b, p_n, p_p, p_next) in snaps:
+            _, s = net.forward(g, b, p_n, p_p, geo.flags)
+            target = ((p_next - p_n) / s).to(torch.float32)
+            net.train_step(g, b, p_n, p_p, target, 2e-3, geo.flags)
+    solver.attach_guess(net)
+    ratios, used = [], 0
+    for n in range(12):
+        s = solver.step(st)
+        assert s.status == 0 and s.relres <= 1e-6
+        if s.relres0 > 0:
+            ratios.append(s.relres_guess / s.relres0)
+            used += s.guess_used
+    assert len(ratios) >= 10
+    assert np.median(ratios) < 1.0 and used >= len(ratios) // 2, ratios
+    solver.attach_guess(None)
+    net.close()

@@ -559,3 +559,34 @@ def test_forces_constant_pressure_and_archimedes():
     V = 4.0 / 3.0 * np.pi * R ** 3
     assert out[0] == pytest.approx(-V, rel=0.06)
     assert abs(out[1]) < 0.03 * V and abs(out[2]) < 0.03 * V
+
+
+# --------------------------------------------------------------------------------------------------
+# QUICK blending of the advective face value (the hybrid scheme of Sec. 3.1 / 3.3)
+
+@pytest.mark.parametrize("Uval", [1.0, -1.0])
+@pytest.mark.parametrize("gamma", [0.0, 0.1, 1.0])
+def test_quick_blend_closed_form_on_a_cubic(Uval, gamma):
+    """u_x = x^3 advected by a uniform U: the face-flux difference is 3x^2 + 1 for central values and
+    3x^2 + 1/4 for QUICK's (6 upwind + 3 downwind - far upwind)/8, so H_x = -U (3x^2 + 1 - 3 gamma / 4)."""
+    nx, ny, nz = 14, 4, 4
+    case = oracle.Case(nx, ny, nz, nu=0.0, dt=0.1, bc=(3, 3, 0, 0, 0, 0), csm_on=0, quick=gamma)
+    xc = np.arange(nx) + 0.5
+    ux = np.broadcast_to(xc ** 3, (nz, ny, nx))
+    u = np.stack([ux, 0 * ux, 0 * ux]).reshape(-1)
+    U = np.zeros(case.NF)
+    Ux, _, _ = oracle.split_faces(U, nx, ny, nz)
+    Ux[...] = Uval
+    H, _ = case.predict(u, U, np.zeros(case.N), np.zeros_like(u), True)
+    Hx = H[:case.N].reshape(nz, ny, nx)
+    exp = -Uval * (3 * xc ** 2 + 1.0 - 0.75 * gamma)
+    assert np.allclose(Hx[:, :, 2:-2], np.broadcast_to(exp[2:-2], (nz, ny, nx - 4)), rtol=1e-12, atol=1e-9)
+
+
+def test_quick_blend_conserves_momentum_periodic():
+    n = 8
+    rng = np.random.default_rng(11)
+    case = oracle.Case(n, n, n, nu=0.02, dt=0.1, bc=PER, quick=0.1)
+    u = rng.standard_normal(3 * n ** 3)
+    H, _ = case.predict(u, case.faces(u), case.csm(u), np.zeros_like(u), True)
+    assert np.all(np.abs(H.reshape(3, -1).sum(1)) < 1e-11 * np.abs(H).sum())

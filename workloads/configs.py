@@ -37,6 +37,7 @@ class Config:
     soup: Optional[Callable] = None
     seed: int = 0
     a_ref: float = 1.0
+    quick: float = 0.0
     note: str = ""
 
     @property
