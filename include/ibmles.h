@@ -45,6 +45,7 @@ typedef enum {
 enum { IBM_BC_PERIODIC = 0, IBM_BC_INFLOW = 1, IBM_BC_OUTFLOW = 2, IBM_BC_SLIP = 3, IBM_BC_NOSLIP = 4 };
 enum { IBM_FP64 = 0, IBM_FP32_REFINE64 = 1 };
 enum { IBM_SOLVER_CG = 0, IBM_SOLVER_BICGSTAB = 1, IBM_SOLVER_RBSOR = 2 };
+enum { IBM_ADAMS_BASHFORTH = 0, IBM_CRANK_NICOLSON = 1 };
 
 typedef struct { int32_t nx, ny, nz, reserved; double dx; } ibm_grid;
 
@@ -73,6 +74,11 @@ typedef struct {
     int32_t mg_sweeps;   /* red-black Gauss-Seidel sweeps before and after each coarse correction (0 = 2) */
     double mg_omega;     /* multigrid coarse-correction factor in (0, 2) (0 = 1.6) */
     double quick;        /* fraction of QUICK in the advected face value, [0, 1] (Sec. 3.1/3.3: 0.05-0.1) */
+    int32_t integrator;  /* IBM_ADAMS_BASHFORTH (explicit, Euler first step) or IBM_CRANK_NICOLSON
+                            (Eq. crank-nicolson, implicit momentum solve by BiCGStab) */
+    int32_t mom_max_iter;/* Crank-Nicolson: BiCGStab iteration cap per step (0 = 200) */
+    double mom_tol;      /* Crank-Nicolson: stop at ||r|| <= mom_tol ||dt L(u^n)|| (0 = 1e-6 in
+                            FP32_REFINE64 mode, 1e-10 in FP64 mode) */
 } les_params;
 
 typedef struct {
@@ -85,6 +91,8 @@ typedef struct {
     double fsum[3];      /* momentum added by the IB forcing this step: sum of du * dx^3 */
     double relres0;      /* with a learned guess attached: initial ||b - A p^n|| / ||b|| (else -1) */
     double relres_guess; /* with a learned guess attached: initial residual of the guess (else -1) */
+    int32_t mom_iters;   /* Crank-Nicolson: momentum BiCGStab iterations of the step (0 for AB2) */
+    int32_t reserved;
 } les_stats;
 
 typedef struct ibm_geom ibm_geom;
@@ -153,7 +161,8 @@ void les_destroy(les_state* st);
 /* Face velocity from a cell field with the face rule of les_faces (no mass correction skipped). */
 int les_init_faces(les_state* st, const void* d_u, void* d_U, void* stream);
 
-/* One fractional step (Sec. 2.1 with Adams-Bashforth 2): CSM eddy viscosity, predictor, IB forcing,
+/* One fractional step (Sec. 2.1; Adams-Bashforth 2 or Crank-Nicolson per params.integrator): CSM eddy
+ * viscosity, predictor, IB forcing,
  * face velocities, RHS, pressure solve, correction.  In/out: d_u[3N], d_U[NF], d_p[N] (double; x0
  * of the solve), d_H[3N] (holds H^{n-1} on entry and H^n on exit).  first_step != 0 takes an Euler
  * step.  Host synchronisation: the pressure solve reads its residual every check_every iterations.
@@ -164,9 +173,18 @@ int les_step(les_state* st, void* d_u, void* d_U, double* d_p, void* d_H, int32_
 /* The step's operators, exposed one by one (les_step calls exactly these). */
 /* Eq. Smagorinsky/Q/FCS: nu_t per cell from central velocity gradients (ghost values on cut links). */
 int les_csm(les_state* st, const void* d_u, void* d_nut, void* stream);
-/* Predictor: H = -div(U u) + div((nu + nu_t) grad u) + div(nu_t grad u^T); u* = u + dt(3/2 H - 1/2 Hprev). */
+/* Adams-Bashforth predictor: H = L(u) = -div(U u) + div((nu + nu_t) grad u) + div(nu_t grad u^T);
+ * u* = u + dt(3/2 H - 1/2 Hprev) (u + dt H on the first step). */
 int les_predict(les_state* st, const void* d_u, const void* d_U, const void* d_nut,
                 const void* d_Hprev, void* d_H, void* d_ustar, int32_t first_step, void* stream);
+/* Crank-Nicolson predictor (Eq. crank-nicolson) with U = U^n and nu_t = nu_t(u^n) in both halves:
+ * delta = u* - u solves delta - (dt/2) L_0(delta) = dt L(u), L_0 the linear part of L (ghost values
+ * without wall and inflow velocities), by BiCGStab over the stacked three components from delta = 0.
+ * d_H[3N] receives L(u), d_ustar[3N] the predicted field; *iters (host, may be NULL) the iterations.
+ * Needs a state created with integrator = IBM_CRANK_NICOLSON.  Synchronises every 4 iterations.
+ * Returns IBM_E_NOCONV at mom_max_iter (d_ustar then holds the last iterate), IBM_E_NONFINITE. */
+int les_predict_cn(les_state* st, const void* d_u, const void* d_U, const void* d_nut, void* d_H, void* d_ustar,
+                   int32_t* iters, void* stream);
 /* Eq. forcing_term + Eq. discrete_forcing_term: in-place forcing of d_ustar; fsum (host, may be
  * NULL, synchronises) = momentum added, sum of du * dx^3. */
 int les_forcing(les_state* st, void* d_ustar, double* fsum, void* stream);
@@ -194,21 +212,44 @@ int forces(les_state* st, const float* d_tri, int64_t ntri, const double* d_p, d
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around each kernel group of
  * les_step / poisson_solve.  les_profile(st, 1) enables and resets the counters, (st, 0) disables.
- * les_profile_read (synchronises) fills ms[13] (total milliseconds) and launches[13] per group, in
+ * les_profile_read (synchronises) fills ms[14] (total milliseconds) and launches[14] per group, in
  * the order: csm, predict, forcing, faces, rhs, residual, cg_dir_spmv, cg_update, correct, sor,
  * mg_fine (fine-grid smoothing passes), mg_transfer (fine-grid restriction and prolongation),
- * mg_coarse (everything on the coarse levels, one group per V-cycle). */
+ * mg_coarse (everything on the coarse levels, one group per V-cycle), momentum (the Crank-Nicolson
+ * BiCGStab after its first operator evaluation, which counts as predict). */
 int les_profile(les_state* st, int32_t on);
 int les_profile_read(les_state* st, double* ms, int64_t* launches);
 /* Kernels this state launched since les_create or the last les_profile(st, 1) (host counter). */
 int64_t les_kernel_launches(const les_state* st);
 
 /* ---------------------------------------------------------------------------------------------- */
+/* Surface pressure per triangle side (Eq. force) with the thin-plate filter of Eq. force_filter    */
+/* (Sec. 3.3), which the paper prints garbled.  Reading: a cell centre x of the 2x2x2 block around  */
+/* the centroid X of a triangle takes part in the Shepard average of X's side only if the open      */
+/* segment X-x crosses no other triangle of the soup, so points behind a second surface closer than  */
+/* a cell (the inner faces of a plate thinner than dx, a duplicated skin) are cancelled.  Cp follows */
+/* as (p_side - p_ref) / (U0^2 / 2).                                                                */
+typedef struct ibm_surface ibm_surface;
+/* Bins the triangles (float32 [ntri][3][3], grid units, device; the caller keeps d_tri alive and
+ * unchanged while the object lives) into 2x2x2-cell bins.  Allocates; synchronises `stream`. */
+int ibm_surface_create(const ibm_grid* grid, const float* d_tri, int64_t ntri, void* stream, ibm_surface** out);
+void ibm_surface_destroy(ibm_surface* surf);
+/* Number of (bin, triangle) entries of the binning (for sizing and tests), -1 for NULL. */
+int64_t ibm_surface_bin_entries(const ibm_surface* surf);
+/* d_pside[2 ntri] (device, double) = front (n.(x - X) > 0) and back Shepard pressure of every
+ * triangle, NaN where a side has no point (degenerate or non-finite triangles: both NaN).  zfilter
+ * != 0 applies the filter.  h_out4 (host, may be NULL; synchronises) = sum over the sides that have
+ * a value of -area p n (front) or +area p n (back), and the number of such sides.  No allocation. */
+int ibm_surface_pressure(ibm_surface* surf, const double* d_p, int32_t zfilter, double* d_pside, double* h_out4,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------------------------- */
 /* Learned initial guess of the pressure solve.  Not in the paper: a small 3-D convolutional network  */
 /* (3x3x3 kernels, 8 -> 8 -> 8 -> 1 channels, ReLU) that maps, per cell, the right-hand side b dx^2,  */
 /* the last pressure change p^n - p^{n-1} (both divided by s = RMS of p^n - p^{n-1}) and the solid    */
-/* mask (cells with a cut link) to (p^{n+1} - p^n) / s.  BF16 weights and activations, FP32         */
-/* accumulation on the tensor cores.  Parameters: W1[8][27][8], W2[8][27][8], W3[1][27][8], b1[8],    */
+/* mask (cells with a cut link) to the deviation of p^{n+1} from the linear extrapolation,           */
+/* (p^{n+1} - 2 p^n + p^{n-1}) / s.  BF16 weights and activations, FP32 accumulation on the tensor  */
+/* cores; a zero network leaves the extrapolation.  Parameters: W1[8][27][8], W2[8][27][8], W3[1][27][8], b1[8],    */
 /* b2[8], b3[1] (ibm_net_num_params() floats), tap = 9 (dz+1) + 3 (dy+1) + (dx+1).                    */
 
 int ibm_net_num_params(void);
@@ -222,14 +263,15 @@ int ibm_net_get_grads(const ibm_net* net, float* h_grads);
  * synchronises) = s.  d_flags may be NULL (no body). */
 int ibm_net_forward(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
                     const double* d_pprev, const uint8_t* d_flags, float* d_out, double* scale, void* stream);
-/* One Adam step (betas 0.9, 0.999) on the mean squared error against d_target[N] = (p^{n+1} - p^n)/s;
+/* One Adam step (betas 0.9, 0.999) on the mean squared error against
+ * d_target[N] = (p^{n+1} - 2 p^n + p^{n-1}) / s;
  * lr = 0 only computes the gradients.  *loss (host, synchronises) = the loss before the update. */
 int ibm_net_train_step(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
                        const double* d_pprev, const uint8_t* d_flags, const float* d_target, float lr,
                        double* loss, void* stream);
 /* Attach (or detach with NULL) a network to a solver state: from the second step on, each les_step
- * starts the pressure solve from p^n + s net(...) when that iterate has the smaller residual, else from
- * p^n.  The state keeps p^{n-1}.  The network must stay alive while attached. */
+ * starts the pressure solve from 2 p^n - p^{n-1} + s net(...) when that iterate has the smaller
+ * residual, else from p^n.  The state keeps p^{n-1}.  The network must stay alive while attached. */
 int les_attach_guess(les_state* st, ibm_net* net);
 /* Copy the right-hand side b of the last les_step / les_rhs into d_b[N]. */
 int les_last_rhs(les_state* st, double* d_b, void* stream);

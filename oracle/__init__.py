@@ -35,12 +35,14 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("u_in", C.c_double * 3),
                 ("bc", C.c_int32 * 6), ("csm_on", C.c_int32), ("forcing_on", C.c_int32),
-                ("deadend_on", C.c_int32), ("pad_", C.c_int32), ("quick", C.c_double)]
+                ("deadend_on", C.c_int32), ("integrator", C.c_int32), ("quick", C.c_double),
+                ("mom_tol", C.c_double), ("mom_maxit", C.c_int32), ("pad_", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
-                ("bnorm", C.c_double), ("fsum", C.c_double * 3)]
+                ("bnorm", C.c_double), ("fsum", C.c_double * 3), ("mom_iters", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 def build(force=False):
@@ -75,6 +77,9 @@ def lib():
         L.or_velocity_across.argtypes = [P, P, P, P, P, P, C.c_int, i64, C.c_int, C.c_int]
         L.or_csm.argtypes = [P, P, P, P, P, P, P]
         L.or_predict.argtypes = [P, P, P, P, P, P, P, P, P, P, P, C.c_int]
+        L.or_momentum_operator.argtypes = [P, P, P, P, P, P, P, P, C.c_int, P]
+        L.or_predict_cn.restype = C.c_int
+        L.or_predict_cn.argtypes = [P, P, P, P, P, P, P, P, P, P, C.c_double, C.c_int32]
         L.or_forcing.argtypes = [P, P, P, P, i64, P, P, P]
         L.or_faces.argtypes = [P, P, P, P, P]
         L.or_rhs.argtypes = [P, P, P, P]
@@ -86,6 +91,7 @@ def lib():
         L.or_step.argtypes = [P, P, P, P, i64, P, P, P, P, P, C.c_int, C.c_double, C.c_int32,
                               C.c_int32, C.c_double, P]
         L.or_forces.argtypes = [P, P, i64, P, P]
+        L.or_surface_pressure.argtypes = [P, P, i64, P, C.c_int, P, P]
         _lib = L
     return _lib
 
@@ -114,13 +120,14 @@ class Case:
     """Grid + physics parameters + (optionally) a classified geometry, all held by the oracle."""
 
     def __init__(self, nx, ny, nz, dx=1.0, nu=0.0, dt=1.0, bc=(0, 0, 0, 0, 0, 0),
-                 u_in=(1.0, 0.0, 0.0), csm_on=1, forcing_on=1, deadend_on=0, quick=0.0):
+                 u_in=(1.0, 0.0, 0.0), csm_on=1, forcing_on=1, deadend_on=0, quick=0.0,
+                 integrator=0, mom_tol=1e-12, mom_maxit=1000):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = nx * ny * nz
         self.NF = nfaces(nx, ny, nz)
         self.g = Grid(nx, ny, nz, 0, dx)
         self.pr = Params(nu, dt, (C.c_double * 3)(*u_in), (C.c_int32 * 6)(*bc), csm_on,
-                         forcing_on, deadend_on, 0, quick)
+                         forcing_on, deadend_on, integrator, quick, mom_tol, mom_maxit, 0)
         self.flags = np.zeros(self.N, np.uint8)
         self.rec = np.zeros(0, RECORD_DTYPE)
         self.cellrec = np.full(self.N, -1, np.int64)
@@ -130,7 +137,7 @@ class Case:
     @classmethod
     def from_config(cls, cfg):
         return cls(cfg.nx, cfg.ny, cfg.nz, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
-                   cfg.forcing_on, cfg.deadend_on, cfg.quick)
+                   cfg.forcing_on, cfg.deadend_on, cfg.quick, cfg.integrator)
 
     # -- geometry ------------------------------------------------------------------------------
     def classify(self, tri, eps_edge=1e-9, eps_det=0.0):
@@ -198,6 +205,25 @@ class Case:
                          int(first_step))
         return H, us
 
+    def momentum_operator(self, u, U, nut, hom=False):
+        """L(u) (per unit volume) with U and nu_t fixed; hom drops the wall and inflow velocities."""
+        u = np.ascontiguousarray(u, np.float64)
+        U = np.ascontiguousarray(U, np.float64)
+        nut = np.ascontiguousarray(nut, np.float64)
+        out = np.zeros(3 * self.N)
+        lib().or_momentum_operator(*self._args(), _p(u), _p(U), _p(nut), int(bool(hom)), _p(out))
+        return out
+
+    def predict_cn(self, u, U, nut, tol=1e-12, maxit=1000):
+        """Crank-Nicolson predictor; returns (H = L(u^n), u*, BiCGStab iterations or -1)."""
+        u = np.ascontiguousarray(u, np.float64)
+        U = np.ascontiguousarray(U, np.float64)
+        nut = np.ascontiguousarray(nut, np.float64)
+        H = np.zeros(3 * self.N)
+        us = np.zeros(3 * self.N)
+        it = lib().or_predict_cn(*self._args(), _p(u), _p(U), _p(nut), _p(H), _p(us), tol, maxit)
+        return H, us, it
+
     def forcing(self, ustar):
         ustar = np.ascontiguousarray(ustar, np.float64)
         out = np.zeros(3 * self.N)
@@ -264,6 +290,17 @@ class Case:
         out = np.zeros(4)
         lib().or_forces(C.byref(self.g), _p(tri), len(tri), _p(p), _p(out))
         return out
+
+    def surface_pressure(self, tri, p, zfilter=True):
+        """Per-triangle (front, back) Shepard pressures (NaN where a side has no point) and the force
+        summed over the sides that have a value; zfilter applies the thin-plate filter."""
+        tri = np.ascontiguousarray(tri, np.float32)
+        p = np.ascontiguousarray(p, np.float64)
+        pside = np.zeros((len(tri), 2))
+        out = np.zeros(4)
+        lib().or_surface_pressure(C.byref(self.g), _p(tri), len(tri), _p(p), int(bool(zfilter)), _p(pside),
+                                  _p(out))
+        return pside, out
 
     def mt_disagreements(self, tri, eps_edge=1e-9, eps_det=0.0):
         tri = np.ascontiguousarray(tri, np.float32)

@@ -360,14 +360,17 @@ int64_t or_setup(const or_grid* g, uint8_t* flags, const int64_t* face_id, const
 /* ------------------------------------------------------------------------------------------------ */
 /* Values read across a link: neighbour, IB ghost (Eq. q_axis / Neumann), or domain-boundary ghost.   */
 
-double or_velocity_across(const or_grid* g, const or_params* pr, const uint8_t* flags,
-                          const or_record* rec, const int64_t* cellrec, const double* u,
-                          int comp, int64_t P, int a, int s) {
+/* Value of component comp read by P across link (a, s).  hom != 0 drops the inhomogeneous parts of
+ * the ghost values (wall velocity u_IB, inflow velocity), which leaves the linear part used by the
+ * implicit operator of the Crank-Nicolson predictor. */
+static double velocity_across_h(const or_grid* g, const or_params* pr, const uint8_t* flags,
+                                const or_record* rec, const int64_t* cellrec, const double* u,
+                                int comp, int64_t P, int a, int s, int hom) {
     const int64_t N = ncells(g);
     double uP = u[comp * N + P];
     if (is_cut(flags, P, a, s)) {
         const or_record* r = link_record(flags, rec, cellrec, P, a, s);
-        double v = r->c_ib * r->uib[comp] + r->c_p * uP;
+        double v = (hom ? 0.0 : r->c_ib * r->uib[comp]) + r->c_p * uP;
         if (r->opp >= 0) v = v + r->c_o * u[comp * N + r->opp];
         return v;
     }
@@ -375,11 +378,17 @@ double or_velocity_across(const or_grid* g, const or_params* pr, const uint8_t* 
     if (neighbour(g, pr, P, a, s, &Nb)) return u[comp * N + Nb];
     /* Reading of the outer boundary conditions (the paper omits them). */
     switch (bc_of(pr, a, s)) {
-        case OR_BC_INFLOW: return 2.0 * pr->u_in[comp] - uP;
+        case OR_BC_INFLOW: return (hom ? 0.0 : 2.0 * pr->u_in[comp]) - uP;
         case OR_BC_OUTFLOW: return uP;
         case OR_BC_SLIP: return comp == a ? -uP : uP;
         default: return -uP; /* no-slip */
     }
+}
+
+double or_velocity_across(const or_grid* g, const or_params* pr, const uint8_t* flags,
+                          const or_record* rec, const int64_t* cellrec, const double* u,
+                          int comp, int64_t P, int a, int s) {
+    return velocity_across_h(g, pr, flags, rec, cellrec, u, comp, P, a, s, 0);
 }
 
 static double p_across(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* p,
@@ -391,15 +400,21 @@ static double p_across(const or_grid* g, const or_params* pr, const uint8_t* fla
 }
 
 /* grad[a][b] = d u_b / d x_a by central differences through the link values. */
+static void velocity_gradient_h(const or_grid* g, const or_params* pr, const uint8_t* flags,
+                                const or_record* rec, const int64_t* cellrec, const double* u,
+                                int64_t P, double grad[3][3], int hom) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double up = velocity_across_h(g, pr, flags, rec, cellrec, u, b, P, a, +1, hom);
+            double um = velocity_across_h(g, pr, flags, rec, cellrec, u, b, P, a, -1, hom);
+            grad[a][b] = (up - um) / (2.0 * g->dx);
+        }
+}
+
 static void velocity_gradient(const or_grid* g, const or_params* pr, const uint8_t* flags,
                               const or_record* rec, const int64_t* cellrec, const double* u,
                               int64_t P, double grad[3][3]) {
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            double up = or_velocity_across(g, pr, flags, rec, cellrec, u, b, P, a, +1);
-            double um = or_velocity_across(g, pr, flags, rec, cellrec, u, b, P, a, -1);
-            grad[a][b] = (up - um) / (2.0 * g->dx);
-        }
+    velocity_gradient_h(g, pr, flags, rec, cellrec, u, P, grad, 0);
 }
 
 /* ------------------------------------------------------------------------------------------------ */
@@ -445,7 +460,7 @@ static double face_velocity(const or_grid* g, const double* U, int64_t P, int a,
  * the same value, so the advective fluxes still telescope. */
 static double face_advected(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                             const int64_t* cellrec, const double* u, int comp, int64_t P, int a, int s,
-                            double uP, double uN, double Uf) {
+                            double uP, double uN, double Uf, int hom) {
     const int64_t N = ncells(g);
     double central = 0.5 * (uP + uN);
     if (pr->quick == 0.0) return central;
@@ -454,53 +469,139 @@ static double face_advected(const or_grid* g, const or_params* pr, const uint8_t
     int64_t Lc = s > 0 ? P : Nb, Rc = s > 0 ? Nb : P;
     double uL = u[comp * N + Lc], uR = u[comp * N + Rc], q;
     if (Uf >= 0.0) {
-        double far = or_velocity_across(g, pr, flags, rec, cellrec, u, comp, Lc, a, -1);
+        double far = velocity_across_h(g, pr, flags, rec, cellrec, u, comp, Lc, a, -1, hom);
         q = (6.0 * uL + 3.0 * uR - far) / 8.0;
     } else {
-        double far = or_velocity_across(g, pr, flags, rec, cellrec, u, comp, Rc, a, +1);
+        double far = velocity_across_h(g, pr, flags, rec, cellrec, u, comp, Rc, a, +1, hom);
         q = (6.0 * uR + 3.0 * uL - far) / 8.0;
     }
     return (1.0 - pr->quick) * central + pr->quick * q;
+}
+
+/* L(u) of cell P: flux-form advection with the face velocity U, diffusion with nu + nu_t and the
+ * transpose part of the SGS stress, summed over the six faces and divided by dx (per unit volume).
+ * U and nu_t are held fixed, so L is affine in u; hom != 0 gives its linear part. */
+static void momentum_flux(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                          const int64_t* cellrec, const double* u, const double* U, const double* nut,
+                          int64_t P, int hom, double out[3]) {
+    const int64_t N = ncells(g);
+    const double dx = g->dx, nu = pr->nu;
+    double GP[3][3], h[3] = {0.0, 0.0, 0.0};
+    velocity_gradient_h(g, pr, flags, rec, cellrec, u, P, GP, hom);
+    for (int a = 0; a < 3; ++a)
+        for (int s = -1; s <= 1; s += 2) {
+            double Uf = face_velocity(g, U, P, a, s);
+            int64_t Nb = -1;
+            int interior = !is_cut(flags, P, a, s) && neighbour(g, pr, P, a, s, &Nb);
+            double nutf = interior ? 0.5 * (nut[P] + nut[Nb]) : nut[P];
+            double GN[3][3];
+            if (interior) velocity_gradient_h(g, pr, flags, rec, cellrec, u, Nb, GN, hom);
+            for (int i = 0; i < 3; ++i) {
+                double uP = u[i * N + P];
+                double uN = velocity_across_h(g, pr, flags, rec, cellrec, u, i, P, a, s, hom);
+                double D1 = (uN - uP) / dx;
+                /* transpose part of 2 S: (d u_a / d x_i) on the face, oriented along +e_a */
+                double T;
+                if (i == a) T = D1;
+                else if (interior) T = (double)s * 0.5 * (GP[i][a] + GN[i][a]);
+                else T = (double)s * GP[i][a];
+                double conv = -(double)s * Uf * face_advected(g, pr, flags, rec, cellrec, u, i, P, a, s, uP, uN, Uf, hom);
+                h[i] += conv + (nu + nutf) * D1 + nutf * T;
+            }
+        }
+    for (int i = 0; i < 3; ++i) out[i] = h[i] / dx;
+}
+
+void or_momentum_operator(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                          const int64_t* cellrec, const double* u, const double* U, const double* nut,
+                          int hom, double* L) {
+    const int64_t N = ncells(g);
+    for (int64_t P = 0; P < N; ++P) {
+        double h[3];
+        momentum_flux(g, pr, flags, rec, cellrec, u, U, nut, P, hom, h);
+        for (int i = 0; i < 3; ++i) L[i * N + P] = h[i];
+    }
 }
 
 void or_predict(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 const int64_t* cellrec, const double* u, const double* U, const double* nut,
                 const double* Hprev, double* H, double* ustar, int first_step) {
     const int64_t N = ncells(g);
-    const double dx = g->dx, nu = pr->nu, dt = pr->dt;
-    for (int64_t P = 0; P < N; ++P) {
-        double GP[3][3], h[3] = {0.0, 0.0, 0.0};
-        velocity_gradient(g, pr, flags, rec, cellrec, u, P, GP);
-        for (int a = 0; a < 3; ++a)
-            for (int s = -1; s <= 1; s += 2) {
-                double Uf = face_velocity(g, U, P, a, s);
-                int64_t Nb = -1;
-                int interior = !is_cut(flags, P, a, s) && neighbour(g, pr, P, a, s, &Nb);
-                double nutf = interior ? 0.5 * (nut[P] + nut[Nb]) : nut[P];
-                double GN[3][3];
-                if (interior) velocity_gradient(g, pr, flags, rec, cellrec, u, Nb, GN);
-                for (int i = 0; i < 3; ++i) {
-                    double uP = u[i * N + P];
-                    double uN = or_velocity_across(g, pr, flags, rec, cellrec, u, i, P, a, s);
-                    double D1 = (uN - uP) / dx;
-                    /* transpose part of 2 S: (d u_a / d x_i) on the face, oriented along +e_a */
-                    double T;
-                    if (i == a) T = D1;
-                    else if (interior) T = (double)s * 0.5 * (GP[i][a] + GN[i][a]);
-                    else T = (double)s * GP[i][a];
-                    double conv = -(double)s * Uf * face_advected(g, pr, flags, rec, cellrec, u, i, P, a, s, uP, uN, Uf);
-                    h[i] += conv + (nu + nutf) * D1 + nutf * T;
-                }
-            }
+    const double dt = pr->dt;
+    or_momentum_operator(g, pr, flags, rec, cellrec, u, U, nut, 0, H);
+    for (int64_t P = 0; P < N; ++P)
         for (int i = 0; i < 3; ++i) {
-            double hi = h[i] / dx, uP = u[i * N + P];
-            H[i * N + P] = hi;
+            double hi = H[i * N + P], uP = u[i * N + P];
             if (first_step)
                 ustar[i * N + P] = uP + dt * hi;
             else
                 ustar[i * N + P] = uP + dt * (1.5 * hi - 0.5 * Hprev[i * N + P]);
         }
+}
+
+/* Crank-Nicolson predictor (Eq. crank-nicolson): (u* - u^n)/dt = (L(u*) + L(u^n))/2 with U = U^n and
+ * nu_t = nu_t(u^n) in both halves.  With delta = u* - u^n and L_0 the linear part of L this is
+ *   M delta = delta - (dt/2) L_0(delta) = dt L(u^n),
+ * one system over the stacked three components (the transpose SGS term couples them), solved by
+ * BiCGStab (the paper's Krylov solver) from delta = 0 to ||dt L(u^n) - M delta|| <= tol ||dt L(u^n)||.
+ * H receives L(u^n).  Returns the BiCGStab iterations, or -1 if maxit was reached. */
+static void cn_matvec(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                      const int64_t* cellrec, const double* U, const double* nut, const double* x, double* y) {
+    const int64_t n3 = 3 * ncells(g);
+    or_momentum_operator(g, pr, flags, rec, cellrec, x, U, nut, 1, y);
+    for (int64_t i = 0; i < n3; ++i) y[i] = x[i] - 0.5 * pr->dt * y[i];
+}
+
+int or_predict_cn(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                  const int64_t* cellrec, const double* u, const double* U, const double* nut, double* H,
+                  double* ustar, double tol, int32_t maxit) {
+    const int64_t n3 = 3 * ncells(g);
+    double* b = (double*)malloc((size_t)n3 * sizeof(double));
+    double* x = (double*)calloc((size_t)n3, sizeof(double));
+    double* r = (double*)malloc((size_t)n3 * sizeof(double));
+    double* rh = (double*)malloc((size_t)n3 * sizeof(double));
+    double* p = (double*)calloc((size_t)n3, sizeof(double));
+    double* v = (double*)calloc((size_t)n3, sizeof(double));
+    double* sv = (double*)malloc((size_t)n3 * sizeof(double));
+    double* t = (double*)malloc((size_t)n3 * sizeof(double));
+    or_momentum_operator(g, pr, flags, rec, cellrec, u, U, nut, 0, H);
+    for (int64_t i = 0; i < n3; ++i) b[i] = pr->dt * H[i];
+    double bn = 0.0;
+    for (int64_t i = 0; i < n3; ++i) bn += b[i] * b[i];
+    bn = sqrt(bn);
+    int it = 0, ok = 1;
+    memcpy(r, b, (size_t)n3 * sizeof(double));          /* x0 = 0 */
+    memcpy(rh, r, (size_t)n3 * sizeof(double));
+    double rho = 1.0, alpha = 1.0, omega = 1.0, rn = bn;
+    while (bn > 0.0 && rn > tol * bn) {
+        if (it >= maxit) { ok = 0; break; }
+        double rho1 = 0.0;
+        for (int64_t i = 0; i < n3; ++i) rho1 += rh[i] * r[i];
+        double beta = (rho1 / rho) * (alpha / omega);
+        for (int64_t i = 0; i < n3; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        cn_matvec(g, pr, flags, rec, cellrec, U, nut, p, v);
+        double rv = 0.0;
+        for (int64_t i = 0; i < n3; ++i) rv += rh[i] * v[i];
+        alpha = rho1 / rv;
+        for (int64_t i = 0; i < n3; ++i) sv[i] = r[i] - alpha * v[i];
+        cn_matvec(g, pr, flags, rec, cellrec, U, nut, sv, t);
+        double ts = 0.0, tt = 0.0;
+        for (int64_t i = 0; i < n3; ++i) { ts += t[i] * sv[i]; tt += t[i] * t[i]; }
+        omega = tt > 0.0 ? ts / tt : 0.0;
+        rn = 0.0;
+        for (int64_t i = 0; i < n3; ++i) {
+            x[i] += alpha * p[i] + omega * sv[i];
+            r[i] = sv[i] - omega * t[i];
+            rn += r[i] * r[i];
+        }
+        rn = sqrt(rn);
+        rho = rho1;
+        ++it;
+        if (omega == 0.0) break;
     }
+    for (int64_t i = 0; i < n3; ++i) ustar[i] = u[i] + x[i];
+    free(b); free(x); free(r); free(rh); free(p); free(v); free(sv); free(t);
+    return ok ? it : -1;
 }
 
 /* ------------------------------------------------------------------------------------------------ */
@@ -838,7 +939,17 @@ int or_step(const or_grid* g, const or_params* pr, const uint8_t* flags, const o
     double* Us = (double*)malloc((size_t)NF * sizeof(double));
     double* b = (double*)malloc((size_t)N * sizeof(double));
     if (pr->csm_on) or_csm(g, pr, flags, rec, cellrec, u, nut);
-    or_predict(g, pr, flags, rec, cellrec, u, U, nut, Hprev, H, us, first_step);
+    st->mom_iters = 0;
+    if (pr->integrator == OR_CRANK_NICOLSON) {
+        st->mom_iters = or_predict_cn(g, pr, flags, rec, cellrec, u, U, nut, H, us, pr->mom_tol, pr->mom_maxit);
+        if (st->mom_iters < 0) {
+            free(nut); free(H); free(us); free(us2); free(Us); free(b);
+            st->status = 4;
+            return 4;
+        }
+    } else {
+        or_predict(g, pr, flags, rec, cellrec, u, U, nut, Hprev, H, us, first_step);
+    }
     memcpy(Hprev, H, (size_t)(3 * N) * sizeof(double));
     st->fsum[0] = st->fsum[1] = st->fsum[2] = 0.0;
     if (pr->forcing_on && nrec > 0) {
@@ -908,4 +1019,111 @@ void or_forces(const or_grid* g, const float* tri, int64_t ntri, const double* p
     out[1] = F[1];
     out[2] = F[2];
     out[3] = (double)used;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Surface pressure per triangle side (Eq. force) with the thin-plate filter Z (Eq. force_filter).    */
+/* Reading of the garbled filter: a surrounding cell centre x^(k) takes part in the Shepard average    */
+/* of surface node X only if X is the first surface that x^(k) sees towards X, i.e. the open segment  */
+/* from X to x^(k) crosses no other triangle (then |X - x| + |x^(k) - X^(k)| is one link length with  */
+/* X^(k) = X).  Points behind a second surface closer than a cell -- the inner faces of a plate       */
+/* thinner than dx, a duplicated skin -- are cancelled.  Each side is averaged on its own; a side     */
+/* left without points has no value (NaN) and adds nothing to the force.                            */
+
+/* orient3d(a, b, c, d) = det[b - a; c - a; d - a], each product and sum rounded once, in this order. */
+static double orient3(const double a[3], const double b[3], const double c[3], const double d[3]) {
+    double u0 = b[0] - a[0], u1 = b[1] - a[1], u2 = b[2] - a[2];
+    double v0 = c[0] - a[0], v1 = c[1] - a[1], v2 = c[2] - a[2];
+    double w0 = d[0] - a[0], w1 = d[1] - a[1], w2 = d[2] - a[2];
+    double m0 = v1 * w2 - v2 * w1;
+    double m1 = v0 * w2 - v2 * w0;
+    double m2 = v0 * w1 - v1 * w0;
+    return (u0 * m0 - u1 * m1) + u2 * m2;
+}
+
+/* The open segment X-Y crosses triangle ABC: X and Y strictly on opposite sides of its plane and the */
+/* line through them inside or on the triangle's edges. */
+static int segment_crosses(const double X[3], const double Y[3], const double A[3], const double B[3],
+                           const double C[3]) {
+    double o1 = orient3(A, B, C, X), o2 = orient3(A, B, C, Y);
+    if (!((o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0))) return 0;
+    double e0 = orient3(X, Y, A, B), e1 = orient3(X, Y, B, C), e2 = orient3(X, Y, C, A);
+    return (e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0) || (e0 <= 0.0 && e1 <= 0.0 && e2 <= 0.0);
+}
+
+void or_surface_pressure(const or_grid* g, const float* tri, int64_t ntri, const double* p, int zfilter,
+                         double* pside, double out[4]) {
+    double F[3] = {0, 0, 0};
+    int64_t sides = 0;
+    for (int64_t t = 0; t < ntri; ++t) {
+        pside[2 * t] = NAN;
+        pside[2 * t + 1] = NAN;
+        double A[3], B[3], C[3];
+        if (!tri_load(tri + 9 * t, A, B, C)) continue;
+        double e1[3], e2[3], n[3], X[3];
+        for (int d = 0; d < 3; ++d) {
+            e1[d] = B[d] - A[d];
+            e2[d] = C[d] - A[d];
+            X[d] = (A[d] + B[d] + C[d]) / 3.0;
+        }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0.0)) continue;
+        double area = 0.5 * len * g->dx * g->dx;
+        for (int d = 0; d < 3; ++d) n[d] /= len;
+        int64_t base[3];
+        for (int d = 0; d < 3; ++d) base[d] = (int64_t)floor(X[d] - 0.5);
+        double sw[2] = {0, 0}, sp[2] = {0, 0};
+        for (int dk = 0; dk < 2; ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+                for (int di = 0; di < 2; ++di) {
+                    int64_t x[3] = {base[0] + di, base[1] + dj, base[2] + dk};
+                    if (x[0] < 0 || x[1] < 0 || x[2] < 0 || x[0] >= g->nx || x[1] >= g->ny || x[2] >= g->nz)
+                        continue;
+                    double Y[3], r2 = 0.0, sd = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        Y[d] = (double)x[d] + 0.5;
+                        double r = Y[d] - X[d];
+                        r2 += r * r;
+                        sd += n[d] * r;
+                    }
+                    if (sd == 0.0) continue;
+                    if (zfilter) {
+                        int hidden = 0;
+                        for (int64_t o = 0; o < ntri && !hidden; ++o) {
+                            if (o == t) continue;
+                            double P0[3], P1[3], P2[3];
+                            if (!tri_load(tri + 9 * o, P0, P1, P2)) continue;
+                            /* a triangle whose bounding box misses the segment's cannot cross it */
+                            int apart = 0;
+                            for (int d = 0; d < 3; ++d) {
+                                double smn = fmin(X[d], Y[d]), smx = fmax(X[d], Y[d]);
+                                double tmn = fmin(fmin(P0[d], P1[d]), P2[d]), tmx = fmax(fmax(P0[d], P1[d]), P2[d]);
+                                if (tmx < smn || tmn > smx) apart = 1;
+                            }
+                            if (!apart) hidden = segment_crosses(X, Y, P0, P1, P2);
+                        }
+                        if (hidden) continue;
+                    }
+                    if (r2 < 1e-24) r2 = 1e-24;
+                    double w = 1.0 / r2;
+                    int side = sd > 0.0 ? 0 : 1;           /* 0 front, 1 back */
+                    sw[side] += w;
+                    sp[side] += w * p[cell_at(g, x)];
+                }
+        for (int sd = 0; sd < 2; ++sd) {
+            if (sw[sd] == 0.0) continue;
+            double ps = sp[sd] / sw[sd];
+            pside[2 * t + sd] = ps;
+            /* pressure pushes on the front side along -n, on the back side along +n */
+            for (int d = 0; d < 3; ++d) F[d] += (sd == 0 ? -1.0 : 1.0) * area * ps * n[d];
+            ++sides;
+        }
+    }
+    out[0] = F[0];
+    out[1] = F[1];
+    out[2] = F[2];
+    out[3] = (double)sides;
 }

@@ -23,6 +23,7 @@ typedef struct { int32_t nx, ny, nz, pad_; double dx; } or_grid;
 
 enum { OR_BC_PERIODIC = 0, OR_BC_INFLOW = 1, OR_BC_OUTFLOW = 2, OR_BC_SLIP = 3, OR_BC_NOSLIP = 4 };
 enum { OR_SOLVER_BICGSTAB = 0, OR_SOLVER_CG = 1, OR_SOLVER_RBSOR = 2 };
+enum { OR_ADAMS_BASHFORTH = 0, OR_CRANK_NICOLSON = 1 };
 
 typedef struct {
     double nu;            /* kinematic viscosity (1/Re in the paper's non-dimensional form) */
@@ -32,8 +33,11 @@ typedef struct {
     int32_t csm_on;       /* coherent-structure model on (Sec. 2.3) */
     int32_t forcing_on;   /* distributed forcing on (Eq. discrete_forcing_term) */
     int32_t deadend_on;   /* dead-end filter B (Eq. deadend_filter) */
-    int32_t pad_;
+    int32_t integrator;   /* OR_ADAMS_BASHFORTH (AB2, Euler first step) or OR_CRANK_NICOLSON */
     double quick;         /* weight of the QUICK face value in the advective flux (hybrid scheme), 0..1 */
+    double mom_tol;       /* Crank-Nicolson: relative residual of the momentum solve */
+    int32_t mom_maxit;    /* Crank-Nicolson: BiCGStab iteration cap */
+    int32_t pad_;
 } or_params;
 
 /* One link record: the cut link of cell `cell` in direction side*e_axis (Sec. 2.4.1, Eq. q_axis). */
@@ -56,6 +60,8 @@ typedef struct {
     double relres;       /* ||b - A p|| / ||b|| at exit */
     double bnorm;        /* ||b|| */
     double fsum[3];      /* momentum added by the IB forcing this step, sum over cells of du * dx^3 */
+    int32_t mom_iters;   /* Crank-Nicolson momentum BiCGStab iterations (0 for AB2) */
+    int32_t pad_;
 } or_stats;
 
 /* Classification (Sec. 2.4.1): exact axis-aligned ray/triangle predicate.  Writes flags bits 0-5 and
@@ -87,6 +93,15 @@ void or_csm(const or_grid* g, const or_params* pr, const uint8_t* flags, const o
 void or_predict(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 const int64_t* cellrec, const double* u, const double* U, const double* nut,
                 const double* Hprev, double* H, double* ustar, int first_step);
+/* L(u) per cell (advection + diffusion + SGS stress divergence per unit volume), U and nu_t fixed;
+ * hom != 0 drops the wall and inflow velocities from the ghost values (the linear part of L). */
+void or_momentum_operator(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                          const int64_t* cellrec, const double* u, const double* U, const double* nut,
+                          int hom, double* L);
+/* Crank-Nicolson predictor (Eq. crank-nicolson); returns BiCGStab iterations or -1 at maxit. */
+int or_predict_cn(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                  const int64_t* cellrec, const double* u, const double* U, const double* nut, double* H,
+                  double* ustar, double tol, int32_t maxit);
 void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 int64_t nrec, const double* ustar_in, double* ustar_out, double fsum[3]);
 void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* ustar,
@@ -97,7 +112,8 @@ int or_solve(const or_grid* g, const or_params* pr, const uint8_t* flags, const 
              double tol, int32_t maxit, int32_t solver, double omega, or_stats* st);
 void or_correct(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* ustar,
                 const double* Ustar, const double* p, double* u, double* U);
-/* One fractional step: CSM -> predictor -> forcing -> faces -> RHS -> solve -> correction. */
+/* One fractional step: CSM -> predictor (AB2 or Crank-Nicolson per pr->integrator) -> forcing ->
+ * faces -> RHS -> solve -> correction. */
 int or_step(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
             int64_t nrec, const int64_t* cellrec, double* u, double* U, double* p, double* Hprev,
             int first_step, double tol, int32_t maxit, int32_t solver, double omega, or_stats* st);
@@ -106,6 +122,14 @@ int or_step(const or_grid* g, const or_params* pr, const uint8_t* flags, const o
  * side of every triangle, F = sum_tri A (p_back - p_front) n.  out[0..2] = force, out[3] = the number
  * of triangles that contributed. */
 void or_forces(const or_grid* g, const float* tri, int64_t ntri, const double* p, double out[4]);
+
+/* Surface pressure per triangle side (Eq. force) with, if zfilter, the thin-plate filter of
+ * Eq. force_filter read as: a cell centre counts for node X only if the open segment from X to it
+ * crosses no other triangle.  pside[2t] = front, pside[2t+1] = back Shepard average (NaN if that
+ * side has no point).  out[0..2] = sum over sides with a value of -/+ area p n (front/back),
+ * out[3] = number of such sides. */
+void or_surface_pressure(const or_grid* g, const float* tri, int64_t ntri, const double* p, int zfilter,
+                         double* pside, double out[4]);
 
 #ifdef __cplusplus
 }

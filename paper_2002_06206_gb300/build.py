@@ -1,7 +1,7 @@
 """Build the CUDA library libibmles.so for sm_103a with nvcc (in-tree, no cmake).
 
-Each translation unit compiles in parallel; the classification unit is compiled without FMA
-contraction so that its FP64 predicate rounds every product and sum separately.
+Each translation unit compiles in parallel; the classification and surface-pressure units are compiled
+without FMA contraction so that their FP64 predicates round every product and sum separately.
 """
 import concurrent.futures as cf
 import os
@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibmles.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = {"classify.cu": ["-fmad=false"], "les.cu": [], "poisson.cu": [], "mg.cu": [], "stencil4.cu": [], "learn.cu": [], "api.cu": []}
+SOURCES = {"classify.cu": ["-fmad=false"], "surface.cu": ["-fmad=false"], "les.cu": [], "poisson.cu": [], "mg.cu": [],
+           "stencil4.cu": [], "learn.cu": [], "api.cu": []}
 
 
 def nvcc():

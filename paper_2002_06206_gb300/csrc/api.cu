@@ -122,6 +122,14 @@ static void free_state(les_state* S) {
     cudaFree(S->p_keep);
     cudaFree(S->x_guess);
     cudaFree(S->two_res);
+    cudaFree(S->c.general);
+    if (S->c.cn) {
+        CNWork* w = S->c.cn;
+        cudaFree(w->r); cudaFree(w->rh); cudaFree(w->p); cudaFree(w->v); cudaFree(w->sv); cudaFree(w->tv);
+        cudaFree(w->x); cudaFree(w->sc);
+        cudaFreeHost(w->hsc);
+        free(w);
+    }
     if (S->c.mg) {
         for (int l = 1; l < S->c.mg->nlev; ++l) {
             MGLev& L = S->c.mg->lev[l];
@@ -158,6 +166,10 @@ static int check_params(const les_params* p) {
         return ibm_fail(IBM_E_INVALID, "mg_omega must lie in (0, 2) for a symmetric positive preconditioner");
     if (p->precond && p->mg_sweeps < 0) return ibm_fail(IBM_E_INVALID, "mg_sweeps must be >= 0");
     if (!(p->quick >= 0.0 && p->quick <= 1.0)) return ibm_fail(IBM_E_INVALID, "quick must lie in [0, 1]");
+    if (p->integrator != IBM_ADAMS_BASHFORTH && p->integrator != IBM_CRANK_NICOLSON)
+        return ibm_fail(IBM_E_INVALID, "unknown integrator %d", p->integrator);
+    if (p->integrator == IBM_CRANK_NICOLSON && (!(p->mom_tol >= 0.0) || p->mom_max_iter < 0))
+        return ibm_fail(IBM_E_INVALID, "mom_tol must be >= 0 and mom_max_iter >= 0");
     return IBM_OK;
 }
 
@@ -208,6 +220,8 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     c.nu = p->nu;
     c.dt = p->dt;
     c.quick = p->quick;
+    c.integrator = p->integrator;
+    c.flux_margin = p->quick > 0.0 ? 2 : 1;
     c.csm_on = p->csm_on;
     c.forcing_on = p->forcing_on;
     c.deadend_on = geom ? ibm_geom_deadend(geom) : 0;
@@ -251,6 +265,38 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     }
     memset(S->hfs, 0, 8 * sizeof(double));
     S->c.nlaunch = &S->nlaunch;
+    {
+        int rc1 = build_general_list(S->c, 0);
+        if (rc1) {
+            free_state(S);
+            return rc1;
+        }
+    }
+    if (p->integrator == IBM_CRANK_NICOLSON) {
+        CNWork* w = (CNWork*)calloc(1, sizeof(CNWork));
+        if (!w) {
+            free_state(S);
+            return ibm_fail(IBM_E_NOMEM, "les_create: host allocation");
+        }
+        S->c.cn = w;
+        w->tol = p->mom_tol > 0.0 ? p->mom_tol : (p->precision == IBM_FP64 ? 1e-10 : 1e-6);
+        w->maxit = p->mom_max_iter > 0 ? p->mom_max_iter : 200;
+        ALLOC(w->r, 3 * N * s);
+        ALLOC(w->rh, 3 * N * s);
+        ALLOC(w->p, 3 * N * s);
+        ALLOC(w->v, 3 * N * s);
+        ALLOC(w->sv, 3 * N * s);
+        ALLOC(w->tv, 3 * N * s);
+        ALLOC(w->x, 3 * N * s);
+        ALLOC(w->sc, sizeof(SolveScal));
+        if ((e = cudaMallocHost((void**)&w->hsc, sizeof(SolveScal))) != cudaSuccess ||
+            (e = cudaMemset(w->sc, 0, sizeof(SolveScal))) != cudaSuccess ||
+            (e = cudaMemset(w->p, 0, 3 * N * s)) != cudaSuccess ||
+            (e = cudaMemset(w->v, 0, 3 * N * s)) != cudaSuccess) {
+            free_state(S);
+            return ibm_cuda_check(e, "les_create: crank-nicolson workspace");
+        }
+    }
     if (p->precond == 1) {
         MG* mg = (MG*)calloc(1, sizeof(MG));
         if (!mg) {
@@ -393,6 +439,15 @@ extern "C" int les_predict(les_state* S, const void* u, const void* U, const voi
     return launch_predict(S->c, u, U, nut, Hprev ? Hprev : H, H, ustar, first ? 1 : 0, (cudaStream_t)stream);
 }
 
+extern "C" int les_predict_cn(les_state* S, const void* u, const void* U, const void* nut, void* H, void* ustar,
+                              int32_t* iters, void* stream) {
+    NEED(S); NEED(u); NEED(U); NEED(nut); NEED(H); NEED(ustar);
+    int it = 0;
+    int rc = launch_predict_cn(S->c, u, U, nut, H, ustar, &it, (cudaStream_t)stream);
+    if (iters) *iters = it;
+    return rc;
+}
+
 extern "C" int les_forcing(les_state* S, void* ustar, double* fsum, void* stream) {
     NEED(S); NEED(ustar);
     cudaStream_t s = (cudaStream_t)stream;
@@ -452,9 +507,14 @@ extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int3
         if ((rc = launch_csm(c, u, S->nut, s))) return rc;
         prof_end(c.prof, PS_CSM, s);
     }
-    prof_begin(c.prof, PS_PREDICT, s);
-    if ((rc = launch_predict(c, u, U, S->nut, H, H, S->ustar, first ? 1 : 0, s))) return rc;
-    prof_end(c.prof, PS_PREDICT, s);
+    int mom_iters = 0;
+    if (c.integrator == IBM_CRANK_NICOLSON) {
+        if ((rc = launch_predict_cn(c, u, U, S->nut, H, S->ustar, &mom_iters, s))) return rc;
+    } else {
+        prof_begin(c.prof, PS_PREDICT, s);
+        if ((rc = launch_predict(c, u, U, S->nut, H, H, S->ustar, first ? 1 : 0, s))) return rc;
+        prof_end(c.prof, PS_PREDICT, s);
+    }
     const bool forcing = c.forcing_on && c.D.flags && c.n_inc > 0;
     if (forcing) {
         prof_begin(c.prof, PS_FORCING, s);
@@ -506,6 +566,7 @@ extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int3
         st->relres0 = (r0 >= 0.0 && ps.bnorm > 0.0) ? sqrt(r0) / ps.bnorm : -1.0;
         st->relres_guess = (rg >= 0.0 && ps.bnorm > 0.0) ? sqrt(rg) / ps.bnorm : -1.0;
         for (int q = 0; q < 3; ++q) st->fsum[q] = forcing ? S->hfs[q] : 0.0;
+        st->mom_iters = mom_iters;
     }
     if (prc == IBM_E_NOCONV) return ibm_fail(prc, "les_step: pressure solve did not converge");
     return IBM_OK;

@@ -33,6 +33,7 @@ struct Dom {
     const uint8_t* flags;      // may be null: no body
     const int32_t* cellrec;    // first record of each Omega_inc cell, -1 elsewhere
     const LinkRec* rec;
+    int hom;                   // 1: ghost values without wall and inflow velocities (linear part)
 };
 
 __device__ __forceinline__ int link_bit(int a, int s) { return 2 * a + (s > 0); }
@@ -63,14 +64,14 @@ __device__ __forceinline__ T vel_across(const Dom& D, const T* __restrict__ u, i
     const int bit = link_bit(a, s);
     if (fl & (1u << bit)) {
         const LinkRec& r = link_record(D, P, fl, bit);
-        T v = (T)r.c_ib * (T)r.uib[comp] + (T)r.c_p * uP;
+        T v = (D.hom ? (T)0 : (T)r.c_ib * (T)r.uib[comp]) + (T)r.c_p * uP;
         if (r.opp >= 0) v = v + (T)r.c_o * u[cN + r.opp];
         return v;
     }
     long long off;
     if (nb_offset(D, a, s, xa, off)) return u[cN + P + off];
     switch (D.bc[bit]) {
-        case IBM_BC_INFLOW: return (T)2 * (T)D.u_in[comp] - uP;
+        case IBM_BC_INFLOW: return (D.hom ? (T)0 : (T)2 * (T)D.u_in[comp]) - uP;
         case IBM_BC_OUTFLOW: return uP;
         case IBM_BC_SLIP: return comp == a ? -uP : uP;
         default: return -uP;

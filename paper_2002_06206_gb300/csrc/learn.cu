@@ -283,11 +283,12 @@ __global__ void k_nn_adam(int n, float* __restrict__ p, const float* __restrict_
 }
 
 // x_guess = p + s * out
-__global__ void k_nn_apply(long long N, const double* __restrict__ p, const float* __restrict__ out,
-                           const double* __restrict__ scal, double* __restrict__ xg) {
+// Guess = linear extrapolation 2 p^n - p^{n-1} plus the network's scaled correction.
+__global__ void k_nn_apply(long long N, const double* __restrict__ p, const double* __restrict__ pprev,
+                           const float* __restrict__ out, const double* __restrict__ scal, double* __restrict__ xg) {
     const double s = scal[0];
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
-        xg[c] = p[c] + s * (double)out[c];
+        xg[c] = (2.0 * p[c] - pprev[c]) + s * (double)out[c];
 }
 
 unsigned blocks_n(long long n, int threads) {
@@ -499,7 +500,7 @@ int net_guess(ibm_net* n, const ibm_grid* g, const double* b, const double* p, c
     if (rc) return rc;
     if ((rc = net_forward(n, g, s))) return rc;
     const long long N = (long long)g->nx * g->ny * g->nz;
-    k_nn_apply<<<blocks_n(N, 256), 256, 0, s>>>(N, p, n->out, n->scal, xg);
+    k_nn_apply<<<blocks_n(N, 256), 256, 0, s>>>(N, p, pprev, n->out, n->scal, xg);
     IBM_LAUNCHED("ibm_net: guess");
     return IBM_OK;
 }

@@ -7,6 +7,10 @@
 // the y/z neighbours of a tile are re-read from L1/L2 rather than HBM.
 #include "solver.cuh"
 
+#ifndef IBM_FLUX_MINB
+#define IBM_FLUX_MINB 3
+#endif
+
 namespace {
 
 template <class T>
@@ -88,32 +92,30 @@ __device__ __forceinline__ T face_adv(const Dom& D, const T* __restrict__ u, int
     return ((T)1 - gam) * central + gam * q;
 }
 
-// Momentum predictor: flux-form central advection with the face velocity U, diffusion with
-// nu + nu_t, the transpose part of the SGS stress divergence, Adams-Bashforth 2 in time.  One thread
-// per cell; a cell whose six neighbours and itself have no cut link and which lies off the domain
-// faces reads every value directly (the same formulas as the general path, which goes through the
-// ghost and boundary rules of vel_across).
+// L(u) of a cell per unit volume: flux-form advection with the face velocity U (central value
+// blended with QUICK), diffusion with nu + nu_t, the transpose part of the SGS stress divergence.
+// flux_general applies the ghost and boundary rules of vel_across on every link; flux_fast is the same
+// formulas for a cell where they reduce to direct reads (fast_cell).  With D.hom set the ghost values
+// lose their wall and inflow velocities, which gives the linear part of L.
+
+// The cell and its six neighbours have no cut link and the cell lies at least mrg cells inside every
+// domain face (mrg = 2 with QUICK, whose far-upwind value is two cells away).
+__device__ __forceinline__ bool fast_cell(const Dom& D, long long P, int i, int j, int k, int mrg) {
+    if (i < mrg || i >= D.nx - mrg || j < mrg || j >= D.ny - mrg || k < mrg || k >= D.nz - mrg) return false;
+    if (!D.flags) return true;
+    const uint8_t* f = D.flags;
+    return (f[P] | f[P - 1] | f[P + 1] | f[P - D.sy] | f[P + D.sy] | f[P - D.sz] | f[P + D.sz]) == 0;
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
-                                                 const T* __restrict__ nut, const T* Hprev, T* H,
-                                                 T* __restrict__ ustar, T nu, T dt, int first, T gam) {
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
-    if (i >= D.nx || j >= D.ny) return;
+__device__ __forceinline__ void flux_fast(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
+                                          const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
+                                          int j, int k, T nu, T gam, T (&h)[3]) {
     const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
-    const int n[3] = {D.nx, D.ny, D.nz};
-    const long long P = i + (long long)D.sy * j + D.sz * k;
-    const unsigned fl = flags_at(D, P);
     const int x[3] = {i, j, k};
     const long long o[3] = {1, (long long)D.sy, D.sz};
-    const int mrg = gam != (T)0 ? 2 : 1;    // QUICK reads two cells away
-    bool fast = fl == 0u && i >= mrg && i < D.nx - mrg && j >= mrg && j < D.ny - mrg && k >= mrg && k < D.nz - mrg;
-    if (fast && D.flags) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) fast = fast && D.flags[P - o[a]] == 0 && D.flags[P + o[a]] == 0;
-    }
     const T nutP = nut[P];
-    T h[3] = {0, 0, 0};
-    if (fast) {
+    h[0] = h[1] = h[2] = (T)0;
         T uc[3], un[3][6], GP[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -160,7 +162,20 @@ __global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* _
                     h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
                 }
             }
-    } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] *= invdx;
+}
+
+template <class T>
+__device__ __forceinline__ void flux_general(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
+                                             const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
+                                             int j, int k, T nu, T gam, T (&h)[3]) {
+    const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
+    const int n[3] = {D.nx, D.ny, D.nz};
+    const unsigned fl = flags_at(D, P);
+    const int x[3] = {i, j, k};
+    const T nutP = nut[P];
+    h[0] = h[1] = h[2] = (T)0;
         T GP[3][3];
         grad_at(D, u, P, x, fl, inv2dx, GP);
 #pragma unroll
@@ -201,16 +216,72 @@ __global__ void __launch_bounds__(256) k_predict(Dom D, FaceLayout F, const T* _
                     h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
                 }
             }
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] *= invdx;
+}
+
+__device__ __forceinline__ void cell_coords(const Dom& D, long long P, int& i, int& j, int& k) {
+    k = (int)(P / D.sz);
+    const long long r = P - (long long)k * D.sz;
+    j = (int)(r / D.sy);
+    i = (int)(r - (long long)j * D.sy);
+}
+
+// Calls body(P, i, j, k) for the cells of the current thread: in the fast kernels one cell of a flat
+// (x, y) tile with one plane per block, skipped unless fast_cell (the general kernel takes it); in the
+// general kernels the entries of the list of the other cells, strided over a capped grid.
+template <bool GENERAL, class Body>
+__device__ __forceinline__ void for_flux_cells(const Dom& D, const int32_t* __restrict__ list, long long nlist,
+                                               int mrg, Body body) {
+    if (GENERAL) {
+        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nlist;
+             q += (long long)gridDim.x * blockDim.x) {
+            const long long P = list[q];
+            int i, j, k;
+            cell_coords(D, P, i, j, k);
+            body(P, i, j, k);
+        }
+        return;
     }
+    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
+    if (i >= D.nx || j >= D.ny) return;
+    const long long P = i + (long long)D.sy * j + D.sz * k;
+    if (fast_cell(D, P, i, j, k, mrg)) body(P, i, j, k);
+}
+
+template <bool GENERAL, class T>
+__device__ __forceinline__ void cell_flux(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
+                                          const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
+                                          int j, int k, T nu, T gam, T (&h)[3]) {
+    if (GENERAL) flux_general(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+    else flux_fast(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+}
+
+// Momentum predictor, Adams-Bashforth 2 in time (Euler on the first step).  One thread per cell.
+// Resident blocks of 256 threads per SM the fast FP32 flux kernels are compiled for (register cap).
+template <class T, bool GENERAL>
+struct FluxOcc {
+    static constexpr int value = (sizeof(T) == 4 && !GENERAL) ? IBM_FLUX_MINB : 1;
+};
+
+template <bool GENERAL, class T>
+__global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_predict(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
+                                                 const T* __restrict__ nut, const T* Hprev, T* H,
+                                                 T* __restrict__ ustar, T nu, T dt, int first, T gam,
+                                                 const int32_t* __restrict__ list, long long nlist, int mrg) {
+    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
+        T h[3];
+        cell_flux<GENERAL>(D, F, u, U, nut, P, i, j, k, nu, gam, h);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long oc = c * D.N + P;
-        const T hc = h[c] * invdx;
-        const T uP = u[oc];
-        const T hp = first ? (T)0 : Hprev[oc];
-        H[oc] = hc;
-        ustar[oc] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
-    }
+        for (int c = 0; c < 3; ++c) {
+            const long long oc = c * D.N + P;
+            const T hc = h[c];
+            const T uP = u[oc];
+            const T hp = first ? (T)0 : Hprev[oc];
+            H[oc] = hc;
+            ustar[oc] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
+        }
+    });
 }
 
 // Distributed direct forcing (Eq. forcing_term, Eq. discrete_forcing_term), gathered per Omega_inc
@@ -519,7 +590,287 @@ unsigned lin_blocks(long long n, int threads) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+
+// ---- Crank-Nicolson predictor (Eq. crank-nicolson) -----------------------------------------------
+// delta = u* - u^n solves M delta = delta - (dt/2) L_0(delta) = dt L(u^n) over the stacked three
+// components; BiCGStab from delta = 0, scalars on the device (the same recurrences as the pressure
+// BiCGStab).  Cell kernels loop over a capped grid; per-thread sums run in the working precision and
+// the block and grid sums in FP64.
+
+// The fast kernel of a pair leaves its sums in sc->part; the general kernel, launched after it, adds
+// its own and finishes (so the totals are formed in a fixed order).
+template <class T, bool GENERAL>
+__global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_begin(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
+                                                  const T* __restrict__ nut, T* __restrict__ H, T* __restrict__ r,
+                                                  T* __restrict__ rh, T* __restrict__ x, T nu, T gam, T dt, double tol2,
+                                                  int maxit, SolveScal* sc, double* partials, unsigned* counter,
+                                                  const int32_t* __restrict__ list, long long nlist, int mrg) {
+    T a0 = 0;
+    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
+        T h[3];
+        cell_flux<GENERAL>(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long q = c * D.N + P;
+            const T b = dt * h[c];
+            H[q] = h[c];
+            r[q] = b;
+            rh[q] = b;
+            x[q] = (T)0;
+            a0 += b * b;
+        }
+    });
+    double acc[1] = {(double)a0};
+    grid_reduce<1>(acc, partials, counter, [&](double* t) {
+        if (!GENERAL) {
+            sc->part[0] = t[0];
+            return;
+        }
+        const double bb = t[0] + sc->part[0];
+        sc->bb = bb;
+        sc->rr = bb;
+        sc->rho = bb;
+        sc->rho_old = 1.0;
+        sc->alpha = 1.0;
+        sc->omega = 1.0;
+        sc->target2 = tol2 * bb;
+        sc->iters = 0;
+        sc->maxit = maxit;
+        sc->restart = 1;
+        sc->nonfinite = isfinite(bb) ? 0 : 1;
+        sc->done = (bb == 0.0 || !isfinite(bb)) ? 1 : 0;
+    });
+}
+
+// p = r (first iteration) or r + beta (p - omega v)
+template <class T>
+__global__ void k_cn_p(long long n, const T* __restrict__ r, T* __restrict__ p, const T* __restrict__ v,
+                       const SolveScal* sc) {
+    if (sc->done) return;
+    const bool rs = sc->restart != 0;
+    const T beta = rs ? (T)0 : (T)((sc->rho / sc->rho_old) * (sc->alpha / sc->omega));
+    const T om = rs ? (T)0 : (T)sc->omega;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        p[q] = rs ? r[q] : r[q] + beta * (p[q] - om * v[q]);
+}
+
+// y = M xin = xin - (dt/2) L_0(xin).  mode 0: (w, y) -> alpha = rho / (r_hat, v).  mode 1 (xin = s):
+// (y, s), (y, y) -> omega.
+template <class T, bool GENERAL>
+__global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(Dom D, FaceLayout F, const T* __restrict__ xin,
+                                                  const T* __restrict__ U, const T* __restrict__ nut,
+                                                  T* __restrict__ y, const T* __restrict__ w, T nu, T gam, T hdt,
+                                                  int mode, SolveScal* sc, double* partials, unsigned* counter,
+                                                  const int32_t* __restrict__ list, long long nlist, int mrg) {
+    if (sc->done) return;
+    T a0 = 0, a1 = 0;
+    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
+        T h[3];
+        cell_flux<GENERAL>(D, F, xin, U, nut, P, i, j, k, nu, gam, h);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long q = c * D.N + P;
+            const T xv = xin[q];
+            const T yv = xv - hdt * h[c];
+            y[q] = yv;
+            if (mode == 0) {
+                a0 += w[q] * yv;
+            } else {
+                a0 += yv * xv;
+                a1 += yv * yv;
+            }
+        }
+    });
+    double acc[2] = {(double)a0, (double)a1};
+    grid_reduce<2>(acc, partials, counter, [&](double* t) {
+        if (!GENERAL) {
+            sc->part[0] = t[0];
+            sc->part[1] = t[1];
+            return;
+        }
+        const double t0 = t[0] + sc->part[0], t1 = t[1] + sc->part[1];
+        if (mode == 0) {
+            sc->rv = t0;
+            sc->alpha = t0 != 0.0 ? sc->rho / t0 : 0.0;
+            if (t0 == 0.0 || !isfinite(t0)) {
+                if (!isfinite(t0)) sc->nonfinite = 1;
+                sc->done = 1;                                        // breakdown
+            }
+        } else {
+            sc->ts = t0;
+            sc->tt = t1;
+            sc->omega = t1 > 0.0 ? t0 / t1 : 0.0;
+        }
+    });
+}
+
+// s = r - alpha v
+template <class T>
+__global__ void k_cn_s(long long n, const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ sv,
+                       const SolveScal* sc) {
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        sv[q] = r[q] - alpha * v[q];
+}
+
+// x += alpha p + omega s, r = s - omega t; (r_hat, r), (r, r); convergence test.
+template <class T>
+__global__ void __launch_bounds__(256) k_cn_xr(long long n, const T* __restrict__ p, const T* __restrict__ sv,
+                                               const T* __restrict__ tv, const T* __restrict__ rh, T* __restrict__ x,
+                                               T* __restrict__ r, SolveScal* sc, double* partials, unsigned* counter) {
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha, om = (T)sc->omega;
+    T a0 = 0, a1 = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        x[q] = x[q] + alpha * p[q] + om * sv[q];
+        const T rv = sv[q] - om * tv[q];
+        r[q] = rv;
+        a0 += rh[q] * rv;
+        a1 += rv * rv;
+    }
+    double acc[2] = {(double)a0, (double)a1};
+    grid_reduce<2>(acc, partials, counter, [&](double* t) {
+        sc->rho_old = sc->rho;
+        sc->rho = t[0];
+        sc->rr_old = sc->rr;
+        sc->rr = t[1];
+        sc->restart = 0;
+        sc->iters += 1;
+        if (!isfinite(t[1])) {
+            sc->nonfinite = 1;
+            sc->done = 1;
+        } else if (t[1] <= sc->target2 || sc->iters >= sc->maxit || sc->omega == 0.0 || t[0] == 0.0) {
+            sc->done = 1;
+        }
+    });
+}
+
+template <class T>
+__global__ void k_cn_finish(long long n, const T* __restrict__ u, const T* __restrict__ x, T* __restrict__ ustar) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        ustar[q] = u[q] + x[q];
+}
+
+template <class T>
+int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T* ustar, int* iters, cudaStream_t s) {
+    CNWork& w = *c.cn;
+    Dom Dh = c.D;
+    Dh.hom = 1;
+    const long long n3 = 3 * c.D.N;
+    const unsigned nbv = lin_blocks(n3, 256);
+    T *r = (T*)w.r, *rh = (T*)w.rh, *p = (T*)w.p, *v = (T*)w.v, *sv = (T*)w.sv, *tv = (T*)w.tv, *x = (T*)w.x;
+    const T nu = (T)c.nu, gam = (T)c.quick, dt = (T)c.dt, hdt = (T)(0.5 * c.dt);
+    const int mrg = c.flux_margin;
+    const unsigned ngen = lin_blocks(c.n_general > 0 ? c.n_general : 1, 256);
+    prof_begin(c.prof, PS_PREDICT, s);
+    k_cn_begin<T, false><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol,
+                                                        w.maxit, w.sc, c.partials, c.counter, nullptr, 0, mrg);
+    k_cn_begin<T, true><<<ngen, 256, 0, s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol, w.maxit,
+                                             w.sc, c.partials, c.counter, c.general, c.n_general, mrg);
+    prof_end(c.prof, PS_PREDICT, s);
+    IBM_LAUNCHED("k_cn_begin");
+    IBM_COUNT(c, 2);
+    auto apply = [&](const T* in, T* out, int mode) {
+        k_cn_apply<T, false><<<c.pgrid, c.cg.block, 0, s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc,
+                                                            c.partials, c.counter, nullptr, 0, mrg);
+        k_cn_apply<T, true><<<ngen, 256, 0, s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc, c.partials,
+                                                 c.counter, c.general, c.n_general, mrg);
+    };
+    for (;;) {
+        prof_begin(c.prof, PS_MOMENTUM, s);
+        for (int it = 0; it < 4; ++it) {
+            k_cn_p<T><<<nbv, 256, 0, s>>>(n3, r, p, v, w.sc);
+            apply(p, v, 0);
+            k_cn_s<T><<<nbv, 256, 0, s>>>(n3, r, v, sv, w.sc);
+            apply(sv, tv, 1);
+            k_cn_xr<T><<<nbv, 256, 0, s>>>(n3, p, sv, tv, rh, x, r, w.sc, c.partials, c.counter);
+        }
+        prof_end(c.prof, PS_MOMENTUM, s);
+        IBM_LAUNCHED("crank-nicolson bicgstab");
+        IBM_COUNT(c, 28);
+        IBM_CUDA(cudaMemcpyAsync(w.hsc, w.sc, sizeof(SolveScal), cudaMemcpyDeviceToHost, s));
+        IBM_CUDA(cudaStreamSynchronize(s));
+        if (w.hsc->done) break;
+    }
+    k_cn_finish<T><<<nbv, 256, 0, s>>>(n3, u, x, ustar);
+    IBM_LAUNCHED("k_cn_finish");
+    IBM_COUNT(c, 1);
+    if (iters) *iters = w.hsc->iters;
+    if (w.hsc->nonfinite) return ibm_fail(IBM_E_NONFINITE, "crank-nicolson momentum solve: non-finite residual");
+    if (!(w.hsc->rr <= w.hsc->target2))
+        return ibm_fail(IBM_E_NOCONV, "crank-nicolson momentum solve: relative residual %.3e after %d iterations",
+                        sqrt(w.hsc->rr / (w.hsc->bb > 0 ? w.hsc->bb : 1.0)), w.hsc->iters);
+    return IBM_OK;
+}
+
 }  // namespace
+
+namespace {
+// Order-preserving compaction of the general cells: one block per (y, z) row, ballots over x.
+__global__ void k_list_general(Dom D, int mrg, const unsigned long long* __restrict__ row_off,
+                               int32_t* __restrict__ list) {
+    const int j = blockIdx.x, k = blockIdx.y;
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const long long row = j + (long long)D.ny * k;
+    for (int i0 = 0; i0 < D.nx; i0 += 32) {
+        const int i = i0 + threadIdx.x;
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        const bool g = i < D.nx && !fast_cell(D, P, i, j, k, mrg);
+        const unsigned m = __ballot_sync(0xffffffffu, g);
+        if (g) list[row_off[row] + base + __popc(m & ((1u << threadIdx.x) - 1u))] = (int32_t)P;
+        __syncwarp();
+        if (threadIdx.x == 0) base += __popc(m);
+        __syncwarp();
+    }
+}
+
+__global__ void k_row_counts(Dom D, int mrg, unsigned long long* __restrict__ rc) {
+    const int j = blockIdx.x, k = blockIdx.y;
+    unsigned n = 0;
+    for (int i = threadIdx.x; i < D.nx; i += 32) {
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        n += !fast_cell(D, P, i, j, k, mrg);
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if (threadIdx.x == 0) rc[j + (long long)D.ny * k] = n;
+}
+
+__global__ void k_row_scan(long long nrows, unsigned long long* __restrict__ rc, unsigned long long* total) {
+    // one thread: rows are few (ny * nz) and this runs once per solver state
+    unsigned long long acc = 0;
+    for (long long r = 0; r < nrows; ++r) {
+        const unsigned long long v = rc[r];
+        rc[r] = acc;
+        acc += v;
+    }
+    *total = acc;
+}
+}  // namespace
+
+int build_general_list(LesCtx& c, cudaStream_t s) {
+    const long long nrows = (long long)c.D.ny * c.D.nz;
+    unsigned long long* rc = nullptr;
+    IBM_CUDA(cudaMalloc((void**)&rc, (size_t)(nrows + 1) * sizeof(unsigned long long)));
+    dim3 rows((unsigned)c.D.ny, (unsigned)c.D.nz);
+    k_row_counts<<<rows, 32, 0, s>>>(c.D, c.flux_margin, rc);
+    k_row_scan<<<1, 1, 0, s>>>(nrows, rc, rc + nrows);
+    unsigned long long total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, rc + nrows, sizeof(total), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c.general, (size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    if (e == cudaSuccess && total > 0) {
+        k_list_general<<<rows, 32, 0, s>>>(c.D, c.flux_margin, rc, c.general);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(rc);
+    if (e != cudaSuccess) return ibm_cuda_check(e, "momentum flux: general-cell list");
+    c.n_general = (long long)total;
+    return IBM_OK;
+}
 
 int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
     if (c.prec == IBM_FP64)
@@ -531,20 +882,39 @@ int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
     return IBM_OK;
 }
 
+template <class T>
+static void predict_t(const LesCtx& c, const T* u, const T* U, const T* nut, const T* Hprev, T* H, T* ustar, int first,
+                      cudaStream_t s) {
+    const int mrg = c.flux_margin;
+    k_predict<false, T><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, u, U, nut, Hprev, H, ustar, (T)c.nu, (T)c.dt, first,
+                                                       (T)c.quick, nullptr, 0, mrg);
+    if (c.n_general > 0)
+        k_predict<true, T><<<lin_blocks(c.n_general, 256), 256, 0, s>>>(c.D, c.F, u, U, nut, Hprev, H, ustar,
+                                                                         (T)c.nu, (T)c.dt, first, (T)c.quick,
+                                                                         c.general, c.n_general, mrg);
+}
+
 int launch_predict(const LesCtx& c, const void* u, const void* U, const void* nut, const void* Hprev, void* H,
                    void* ustar, int first, cudaStream_t s) {
     if (c.prec == IBM_FP64)
-        k_predict<double><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const double*)u, (const double*)U,
-                                                         (const double*)nut, (const double*)Hprev, (double*)H,
-                                                         (double*)ustar, c.nu, c.dt, first, c.quick);
+        predict_t<double>(c, (const double*)u, (const double*)U, (const double*)nut, (const double*)Hprev, (double*)H,
+                          (double*)ustar, first, s);
     else
-        k_predict<float><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, (const float*)u, (const float*)U,
-                                                        (const float*)nut, (const float*)Hprev, (float*)H,
-                                                        (float*)ustar, (float)c.nu, (float)c.dt, first,
-                                                        (float)c.quick);
+        predict_t<float>(c, (const float*)u, (const float*)U, (const float*)nut, (const float*)Hprev, (float*)H,
+                         (float*)ustar, first, s);
     IBM_LAUNCHED("k_predict");
-    IBM_COUNT(c, 1);
+    IBM_COUNT(c, c.n_general > 0 ? 2 : 1);
     return IBM_OK;
+}
+
+int launch_predict_cn(const LesCtx& c, const void* u, const void* U, const void* nut, void* H, void* ustar,
+                      int* iters, cudaStream_t s) {
+    if (!c.cn) return ibm_fail(IBM_E_INVALID, "crank-nicolson predictor: state created without integrator = 1");
+    if (c.prec == IBM_FP64)
+        return predict_cn_t<double>(c, (const double*)u, (const double*)U, (const double*)nut, (double*)H,
+                                    (double*)ustar, iters, s);
+    return predict_cn_t<float>(c, (const float*)u, (const float*)U, (const float*)nut, (float*)H, (float*)ustar,
+                               iters, s);
 }
 
 int launch_forcing(const LesCtx& c, void* ustar, cudaStream_t s) {

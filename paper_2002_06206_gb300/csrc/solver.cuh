@@ -11,12 +11,13 @@ struct SolveScal {
     double rz, rz_old;                  // preconditioned CG: (r, z) and its previous value
     int done, iters, restart, nonfinite;
     int maxit, pad0, pad1, pad2;
+    double part[2];                     // partial sums handed from a fast kernel to its general partner
 };
 
 // Optional per-kernel timing with CUDA events on the launching stream (les_profile).
 enum ProfSlot {
     PS_CSM = 0, PS_PREDICT, PS_FORCING, PS_FACES, PS_RHS, PS_RESIDUAL, PS_CG_SPMV, PS_CG_UPDATE, PS_CORRECT,
-    PS_SOR, PS_MG_FINE, PS_MG_TRANSFER, PS_MG_COARSE, PS_COUNT
+    PS_SOR, PS_MG_FINE, PS_MG_TRANSFER, PS_MG_COARSE, PS_MOMENTUM, PS_COUNT
 };
 struct Prof {
     int on;
@@ -50,6 +51,16 @@ struct MG {
     MGLev lev[IBM_MG_MAXLEV];
 };
 
+// Crank-Nicolson predictor workspace: BiCGStab vectors over the stacked three components (3N values
+// of the working precision each) and its device-side scalars.
+struct CNWork {
+    void *r, *rh, *p, *v, *sv, *tv, *x;
+    SolveScal* sc;            // device
+    SolveScal* hsc;           // pinned host copy
+    double tol;
+    int maxit;
+};
+
 struct LesCtx {
     Dom D;
     FaceLayout F;
@@ -71,7 +82,14 @@ struct LesCtx {
     Prof* prof;               // null unless profiling
     long long* nlaunch;       // running count of kernel launches (host memory)
     MG* mg;                   // multigrid preconditioner, null for plain CG
+    int integrator;           // IBM_ADAMS_BASHFORTH or IBM_CRANK_NICOLSON
+    CNWork* cn;               // Crank-Nicolson workspace, null for Adams-Bashforth
+    int flux_margin;          // momentum flux: 2 with QUICK, else 1
+    int32_t* general;         // cells the momentum flux evaluates with the general rules
+    long long n_general;
 };
+// les.cu: list of the cells that are not fast_cell for the momentum flux (c.general, c.n_general).
+int build_general_list(LesCtx& c, cudaStream_t s);
 
 #define IBM_COUNT(c, n) \
     do { if ((c).nlaunch) *(c).nlaunch += (n); } while (0)
@@ -80,6 +98,9 @@ struct LesCtx {
 int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s);
 int launch_predict(const LesCtx& c, const void* u, const void* U, const void* nut, const void* Hprev, void* H,
                    void* ustar, int first, cudaStream_t s);
+// Crank-Nicolson predictor: H = L(u), ustar = u + delta; *iters = momentum BiCGStab iterations.
+int launch_predict_cn(const LesCtx& c, const void* u, const void* U, const void* nut, void* H, void* ustar,
+                      int* iters, cudaStream_t s);
 int launch_forcing(const LesCtx& c, void* ustar, cudaStream_t s);   // sums in c.fscal[0..2]
 int launch_faces(const LesCtx& c, const void* ustar, void* Ustar, cudaStream_t s);
 int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s);

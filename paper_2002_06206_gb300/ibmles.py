@@ -18,6 +18,7 @@ PERIODIC, INFLOW, OUTFLOW, SLIP, NOSLIP = range(5)
 FP64, FP32_REFINE64 = 0, 1
 CG, BICGSTAB, RBSOR = 0, 1, 2
 NO_PRECOND, MULTIGRID = 0, 1
+ADAMS_BASHFORTH, CRANK_NICOLSON = 0, 1
 
 
 class IbmError(RuntimeError):
@@ -42,18 +43,20 @@ class Params(C.Structure):
                 ("solver", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("check_every", C.c_int32), ("inner_tol", C.c_double), ("sor_omega", C.c_double),
                 ("precond", C.c_int32), ("mg_sweeps", C.c_int32), ("mg_omega", C.c_double),
-                ("quick", C.c_double)]
+                ("quick", C.c_double), ("integrator", C.c_int32), ("mom_max_iter", C.c_int32),
+                ("mom_tol", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("status", C.c_int32), ("guess_used", C.c_int32),
                 ("relres", C.c_double), ("bnorm", C.c_double), ("fsum", C.c_double * 3),
-                ("relres0", C.c_double), ("relres_guess", C.c_double)]
+                ("relres0", C.c_double), ("relres_guess", C.c_double), ("mom_iters", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {"iters": self.iters, "outer": self.outer, "status": self.status, "relres": self.relres,
                 "bnorm": self.bnorm, "fsum": list(self.fsum), "guess_used": self.guess_used,
-                "relres0": self.relres0, "relres_guess": self.relres_guess}
+                "relres0": self.relres0, "relres_guess": self.relres_guess, "mom_iters": self.mom_iters}
 
 
 _lib = None
@@ -77,6 +80,8 @@ SIGNATURES = {
     "les_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                            C.c_void_p, C.c_void_p]),
     "les_csm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "les_predict_cn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
     "les_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_int32, C.c_void_p]),
     "les_forcing": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -103,6 +108,10 @@ SIGNATURES = {
                                      C.c_void_p, C.c_float, C.c_void_p, C.c_void_p]),
     "les_attach_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
     "les_last_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ibm_surface_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "ibm_surface_destroy": (None, [C.c_void_p]),
+    "ibm_surface_bin_entries": (C.c_int64, [C.c_void_p]),
+    "ibm_surface_pressure": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ibm_last_error": (C.c_char_p, []),
 }
 
@@ -155,6 +164,42 @@ def make_grid(nx, ny, nz, dx=1.0):
 
 def num_faces(nx, ny, nz):
     return (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
+
+
+class Surface:
+    """Triangle bins for the surface pressure with the thin-plate filter (ibm_surface_*).  Keeps a
+    reference to the soup tensor, which must stay unchanged."""
+
+    def __init__(self, grid, tri, stream=None):
+        self.tri = tri
+        h = C.c_void_p()
+        _check(lib().ibm_surface_create(C.byref(grid), _ptr(tri, torch.float32, "tri"), tri.shape[0],
+                                        _stream(stream), C.byref(h)))
+        self.handle = h
+        self.ntri = tri.shape[0]
+
+    def bin_entries(self):
+        return int(lib().ibm_surface_bin_entries(self.handle))
+
+    def pressure(self, p, zfilter=True, pside=None, stream=None):
+        """Returns (pside[ntri, 2] device tensor, [Fx, Fy, Fz, sides])."""
+        if pside is None:
+            pside = torch.empty((self.ntri, 2), dtype=torch.float64, device=p.device)
+        out = (C.c_double * 4)()
+        _check(lib().ibm_surface_pressure(self.handle, _ptr(p, torch.float64, "p"), int(bool(zfilter)),
+                                          _ptr(pside, torch.float64, "pside"), out, _stream(stream)))
+        return pside, list(out)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ibm_surface_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Geometry:
@@ -229,14 +274,15 @@ class Solver:
 
     def __init__(self, grid, nu, dt, bc, u_in=(1.0, 0.0, 0.0), precision=FP64, solver=CG, tol=1e-6,
                  max_iter=100000, check_every=16, inner_tol=1e-4, sor_omega=1.9, csm_on=1, forcing_on=1,
-                 geometry=None, precond=NO_PRECOND, mg_sweeps=2, mg_omega=1.6, quick=0.0):
+                 geometry=None, precond=NO_PRECOND, mg_sweeps=2, mg_omega=1.6, quick=0.0,
+                 integrator=ADAMS_BASHFORTH, mom_tol=0.0, mom_max_iter=0):
         self.grid = grid
         self.N = grid.nx * grid.ny * grid.nz
         self.NF = num_faces(grid.nx, grid.ny, grid.nz)
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.params = Params(nu, dt, (C.c_double * 3)(*u_in), (C.c_int32 * 6)(*bc), csm_on, forcing_on,
                              precision, solver, tol, max_iter, check_every, inner_tol, sor_omega, precond,
-                             mg_sweeps, mg_omega, quick)
+                             mg_sweeps, mg_omega, quick, integrator, mom_max_iter, mom_tol)
         self.geometry = geometry
         h = C.c_void_p()
         _check(lib().les_create(C.byref(grid), C.byref(self.params),
@@ -276,6 +322,12 @@ class Solver:
                                  _ptr(Hprev, self.dtype), _ptr(H, self.dtype), _ptr(ustar, self.dtype), int(first),
                                  _stream(stream)))
 
+    def predict_cn(self, u, U, nut, H, ustar, stream=None):
+        it = C.c_int32()
+        _check(lib().les_predict_cn(self.handle, _ptr(u, self.dtype), _ptr(U, self.dtype), _ptr(nut, self.dtype),
+                                    _ptr(H, self.dtype), _ptr(ustar, self.dtype), C.byref(it), _stream(stream)))
+        return it.value
+
     def forcing(self, ustar, stream=None):
         fs = (C.c_double * 3)()
         _check(lib().les_forcing(self.handle, _ptr(ustar, self.dtype), fs, _stream(stream)))
@@ -309,14 +361,14 @@ class Solver:
         return list(out)
 
     PROFILE_SLOTS = ("csm", "predict", "forcing", "faces", "rhs", "residual", "cg_dir_spmv", "cg_update",
-                     "correct", "sor", "mg_fine", "mg_transfer", "mg_coarse")
+                     "correct", "sor", "mg_fine", "mg_transfer", "mg_coarse", "momentum")
 
     def profile(self, on):
         _check(lib().les_profile(self.handle, int(on)))
 
     def profile_read(self):
-        ms = (C.c_double * 13)()
-        n = (C.c_int64 * 13)()
+        ms = (C.c_double * len(self.PROFILE_SLOTS))()
+        n = (C.c_int64 * len(self.PROFILE_SLOTS))()
         _check(lib().les_profile_read(self.handle, ms, n))
         return {k: (ms[q], n[q]) for q, k in enumerate(self.PROFILE_SLOTS)}
 

@@ -282,15 +282,52 @@ def test_poisson_nonconvergence_and_nonfinite_are_reported(L):
     assert rc == L.E_NONFINITE
 
 
+@pytest.mark.parametrize("prec,quick,tol", [(0, 0.0, 1e-9), (0, 0.1, 1e-9), (1, 0.1, 2e-5)])
+def test_crank_nicolson_predictor_matches_oracle(L, prec, quick, tol):
+    """Eq. crank-nicolson on identical inputs: inflow, no-slip floor and a moving wall make the ghost
+    values inhomogeneous, so the split into L(u^n) and the linear part L_0 is exercised."""
+    tri = np.concatenate([W.icosphere(3, 7.3, (17.2, 19.6, 18.1)),
+                          W.fan_disk((30.3, 20.1, 17.7), 6.0, 0, 64)]).astype(np.float32)
+    bc = (1, 2, 3, 3, 4, 3)
+    g, geo, ref = both_geometries(L, 48, 40, 36, tri, bc, 0.03, 0.3)
+    ref.pr.quick = quick
+    ref.rec["uib"][:, 0] = 0.3
+    geo.set_boundary_velocity(torch.tensor([[0.3, 0.0, 0.0]], dtype=torch.float64, device="cuda")
+                              .repeat(len(ref.rec), 1).contiguous())
+    mom_tol = 1e-13 if prec == 0 else 1e-6
+    solver = L.Solver(g, 0.03, 0.3, bc, precision=prec, tol=1e-10, geometry=geo, quick=quick,
+                      integrator=L.CRANK_NICOLSON, mom_tol=mom_tol)
+    td = solver.dtype
+    dtype = np.float64 if prec == 0 else np.float32
+    rng = np.random.default_rng(8)
+    u = (np.array([1.0, 0.0, 0.0])[:, None] + 0.3 * rng.standard_normal((3, ref.N))).astype(dtype).reshape(-1)
+    u64 = u.astype(np.float64)
+    U_in = ref.faces(u64).astype(dtype)
+    nut_in = ref.csm(u64).astype(dtype)
+    H = torch.empty(3 * ref.N, dtype=td, device="cuda")
+    us = torch.empty(3 * ref.N, dtype=td, device="cuda")
+    it = solver.predict_cn(_t(u, td), _t(U_in, td), _t(nut_in, td), H, us)
+    H_ref, us_ref, it_ref = ref.predict_cn(u64, U_in.astype(np.float64), nut_in.astype(np.float64), tol=1e-13)
+    assert it > 0 and it_ref > 0
+    assert rel(H.cpu().numpy(), H_ref) <= (1e-12 if prec == 0 else tol)
+    assert rel(us.cpu().numpy(), us_ref) <= tol
+    # the increment itself, which the solve determines, agrees to the solve tolerance
+    d, d_ref = us.cpu().numpy().astype(np.float64) - u64, us_ref - u64
+    assert rel(d, d_ref) <= (1e-9 if prec == 0 else 2e-3)
+
+
 # ------------------------------------------------------------------------------------------------
 # Whole steps
 
-def _run_pair(L, cfg_like, tri, steps, prec, tol, u0, bc, precond=0, solver_kind=0, quick=0.0):
+def _run_pair(L, cfg_like, tri, steps, prec, tol, u0, bc, precond=0, solver_kind=0, quick=0.0, integrator=0,
+              mom_tol=0.0):
     nx, ny, nz, nu, dt = cfg_like
     g, geo, ref = both_geometries(L, nx, ny, nz, tri, bc, nu, dt)
     ref.pr.quick = quick
+    ref.pr.integrator = integrator
+    ref.pr.mom_tol = 1e-13
     solver = L.Solver(g, nu, dt, bc, precision=prec, tol=tol, geometry=geo, precond=precond, solver=solver_kind,
-                      quick=quick)
+                      quick=quick, integrator=integrator, mom_tol=mom_tol)
     st = solver.fields(u0)
     ost = ref.initial_state(u0)
     for _ in range(steps):
@@ -327,6 +364,32 @@ def test_ten_steps_ground_cube_plate_ragged(L, quick):
     cfg = (131, 64, 37, 8.0 / 4e4, 0.2)
     u0 = W.initial_fields(W.Config("c", 131, 64, 37, 0, 0, 0, 0, 0, GROUND, seed=3))
     st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP64, 1e-9, u0, GROUND, quick=quick)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-6
+
+
+@pytest.mark.parametrize("prec,tol,mom_tol", [(0, 1e-8, 1e-13), (1, 1e-4, 1e-6)])
+def test_ten_steps_crank_nicolson_quick(L, prec, tol, mom_tol):
+    """The paper's production configuration: Crank-Nicolson predictor with 10 % QUICK."""
+    if prec == 0:
+        cfg = W.get_config("sphere_64x32x32")
+        u0 = W.initial_fields(cfg)
+        st, ost, _ = _run_pair(L, (cfg.nx, cfg.ny, cfg.nz, cfg.nu, cfg.dt), cfg.soup(), 10, L.FP64, 1e-10, u0,
+                               cfg.bc, 1, 0, 0.1, L.CRANK_NICOLSON, mom_tol)
+    else:
+        tri = W.dirty_sphere(seed=2, radius=6.0, center=(24.0, 24.0, 24.0), subdiv=4)
+        u0 = W.initial_fields(W.Config("d", 96, 48, 48, 0, 0, 0, 0, 0, CHANNEL, seed=2))
+        st, ost, _ = _run_pair(L, (96, 48, 48, 12.0 / 1e4, 0.2), tri, 10, L.FP32_REFINE64, 1e-6, u0, CHANNEL, 1, 0,
+                               0.1, L.CRANK_NICOLSON, mom_tol)
+    assert rel(st["u"].cpu().numpy(), ost["u"]) <= tol
+    assert rel(st["U"].cpu().numpy(), ost["U"]) <= tol
+
+
+def test_ten_steps_crank_nicolson_ground_ragged(L):
+    tri = W.cube_and_plate() * np.float32(0.25)
+    cfg = (131, 64, 37, 8.0 / 4e4, 0.2)
+    u0 = W.initial_fields(W.Config("c", 131, 64, 37, 0, 0, 0, 0, 0, GROUND, seed=3))
+    st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP64, 1e-9, u0, GROUND, quick=0.1, integrator=L.CRANK_NICOLSON,
+                           mom_tol=1e-13)
     assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-6
 
 
@@ -415,3 +478,71 @@ def test_forces_match_oracle_and_closed_forms(L):
     ref_out = ref.forces(bad, np.where(inside, 0.0, X.reshape(-1)))
     assert out[3] == ref_out[3] == len(tri) - 2
     assert np.allclose(out[:3], ref_out[:3], rtol=1e-10)
+
+
+# ------------------------------------------------------------------------------------------------
+# Surface pressure with the thin-plate filter (Eq. force, Eq. force_filter)
+
+def _square(z, lo=3.1, hi=12.9):
+    a, b, c, d = (lo, lo, z), (hi, lo, z), (hi, hi, z), (lo, hi, z)
+    return np.array([[a, b, c], [a, c, d]], np.float32)
+
+
+def _surface_case(L, nx, ny, nz, tri, p, zfilter):
+    g = L.make_grid(nx, ny, nz)
+    S = L.Surface(g, torch.from_numpy(np.ascontiguousarray(tri, np.float32)).cuda())
+    ps, F = S.pressure(_t(p, torch.float64), zfilter=zfilter)
+    ref = oracle.Case(nx, ny, nz)
+    ps_ref, F_ref = ref.surface_pressure(tri, p, zfilter=zfilter)
+    return ps.cpu().numpy(), np.array(F), ps_ref, F_ref, S
+
+
+@pytest.mark.parametrize("zfilter", [True, False])
+def test_surface_pressure_thin_plate_bit_exact(L, zfilter):
+    n = 16
+    x = np.arange(n) + 0.5
+    Z = np.meshgrid(x, x, x, indexing="ij")[0].reshape(-1)
+    p = 2.0 + 0.5 * Z + np.where(Z > 10.25, 1.5, 0.0)
+    tri = np.concatenate([_square(10.2), _square(10.3)])
+    ps, F, ps_ref, F_ref, _ = _surface_case(L, n, n, n, tri, p, zfilter)
+    assert np.array_equal(ps, ps_ref, equal_nan=True)
+    assert F[3] == F_ref[3] and np.allclose(F[:3], F_ref[:3], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("zfilter", [True, False])
+def test_surface_pressure_dirty_sphere_bit_exact(L, zfilter):
+    """The dirty-sphere recipe at D = 12, subdivision 3 (about 2.8k triangles with duplicates, a nested shell, a
+    disk, holes and jitter) on a 48^3 grid, plus non-finite and degenerate triangles."""
+    tri = W.dirty_sphere(seed=2, radius=6.0, center=(24.0, 24.0, 24.0), subdiv=3).copy()
+    tri[5, 1, 2] = np.nan
+    tri[9] = tri[9, 0]
+    n = 48
+    rng = np.random.default_rng(3)
+    x = np.arange(n) + 0.5
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    p = (X + 0.3 * Y).reshape(-1) + 0.1 * rng.standard_normal(n ** 3)
+    ps, F, ps_ref, F_ref, S = _surface_case(L, n, n, n, tri, p, zfilter)
+    assert S.bin_entries() >= len(tri) - 2
+    assert np.array_equal(ps, ps_ref, equal_nan=True)
+    assert np.isnan(ps[5]).all() and np.isnan(ps[9]).all()
+    assert F[3] == F_ref[3]
+    assert np.allclose(F[:3], F_ref[:3], rtol=1e-11, atol=1e-11 * np.abs(F_ref[:3]).max())
+    if zfilter:
+        assert np.isnan(ps).sum() > np.isnan(_surface_case(L, n, n, n, tri, p, False)[0]).sum()
+
+
+def test_surface_pressure_full_size_dirty_sphere_properties(L):
+    """The 256x128x128 dirty sphere (40,602 triangles): uniform pressure is reproduced exactly on every
+    side that keeps a point, and the filter cancels sides only."""
+    cfg = W.get_config("dirty_sphere_256x128x128")
+    tri = cfg.soup()
+    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz)
+    S = L.Surface(g, torch.from_numpy(tri).cuda())
+    p = torch.full((cfg.ncell,), 1.75, dtype=torch.float64, device="cuda")
+    ps1, F1 = S.pressure(p, zfilter=True)
+    ps0, F0 = S.pressure(p, zfilter=False)
+    a1, a0 = ps1.cpu().numpy(), ps0.cpu().numpy()
+    ok = ~np.isnan(a1)
+    assert np.allclose(a1[ok], 1.75, rtol=1e-15, atol=0)
+    assert np.all(np.isnan(a0) <= np.isnan(a1))          # filtering never adds a side
+    assert F1[3] == ok.sum() and F1[3] < F0[3]

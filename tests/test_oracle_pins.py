@@ -590,3 +590,211 @@ def test_quick_blend_conserves_momentum_periodic():
     u = rng.standard_normal(3 * n ** 3)
     H, _ = case.predict(u, case.faces(u), case.csm(u), np.zeros_like(u), True)
     assert np.all(np.abs(H.reshape(3, -1).sum(1)) < 1e-11 * np.abs(H).sum())
+
+
+# --------------------------------------------------------------------------------------------------
+# Crank-Nicolson predictor (Eq. crank-nicolson)
+
+def _face_symbol(theta, Uval, gamma):
+    """Advected value on face i+1/2 relative to u_i for the mode e^{i theta i}: central average
+    blended with QUICK taken from the upwind side."""
+    e = np.exp(1j * theta)
+    central = 0.5 * (1 + e)
+    quick = (6 + 3 * e - 1 / e) / 8 if Uval >= 0 else (6 * e + 3 - e * e) / 8
+    return (1 - gamma) * central + gamma * quick
+
+
+def _fourier_case(gamma, integrator):
+    nx, ny, nz = 16, 12, 4
+    nu, dt = 0.05, 0.4
+    case = oracle.Case(nx, ny, nz, nu=nu, dt=dt, bc=PER, csm_on=0, quick=gamma, integrator=integrator)
+    U = np.zeros(case.NF)
+    Ux, Uy, _ = oracle.split_faces(U, nx, ny, nz)
+    Ux[...] = 0.7
+    Uy[...] = -0.45
+    tx, ty = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    lam = 0.0
+    for th, Uval in ((tx, 0.7), (ty, -0.45)):
+        lam += -Uval * _face_symbol(th, Uval, gamma) * (1 - np.exp(-1j * th))
+        lam += -nu * (2 - 2 * np.cos(th))
+    i = np.arange(nx)[None, None, :]
+    j = np.arange(ny)[None, :, None]
+    phase = tx * i + ty * j + np.zeros((nz, 1, 1))
+    return case, U, lam, phase
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.1])
+def test_crank_nicolson_amplification_of_a_fourier_mode(gamma):
+    """Uniform U = (0.7, -0.45, 0), periodic box, nu_t = 0: every mode e^{i(theta_x i + theta_y j)}
+    is an eigenvector of L with the eigenvalue lam built from the face-value symbols, so the
+    Crank-Nicolson predictor multiplies it by (1 + dt lam / 2) / (1 - dt lam / 2) and the Euler first
+    step by 1 + dt lam."""
+    case, U, lam, phase = _fourier_case(gamma, 1)
+    dt = case.pr.dt
+    comps = [np.cos(phase + q) for q in (0.0, 0.9, 2.1)]
+    u = np.stack(comps).reshape(-1)
+    H, us, it = case.predict_cn(u, U, np.zeros(case.N), tol=1e-14, maxit=200)
+    assert it > 0
+    g = (1 + 0.5 * dt * lam) / (1 - 0.5 * dt * lam)
+    exp = np.stack([np.real(g * np.exp(1j * (phase + q))) for q in (0.0, 0.9, 2.1)]).reshape(-1)
+    assert np.allclose(us, exp, rtol=0, atol=1e-11)
+    # the Euler first step of the explicit path uses the same operator
+    _, ue = case.predict(u, U, np.zeros(case.N), np.zeros_like(u), True)
+    exp_e = np.stack([np.real((1 + dt * lam) * np.exp(1j * (phase + q))) for q in (0.0, 0.9, 2.1)]).reshape(-1)
+    assert np.allclose(ue, exp_e, rtol=0, atol=1e-12)
+    # the scheme is neutral for pure advection and damps with diffusion: |g| < 1 here
+    assert abs(g) < 1.0
+
+
+def test_momentum_operator_is_affine_with_the_homogeneous_part():
+    """With a wall (cut links, moving wall velocity) and an inflow face, L(u) - L(0) equals the
+    homogeneous operator L_0(u) for any u, and L_0 is linear."""
+    case = oracle.Case(14, 10, 9, nu=0.03, dt=0.2, bc=(1, 2, 3, 3, 4, 0), u_in=(1.0, 0.2, -0.1), quick=0.1)
+    tri = W.icosphere(2, 2.6, (6.3, 5.1, 4.4))
+    case.set_geometry(tri)
+    assert len(case.rec) > 0
+    case.rec["uib"][:, 0] = 0.3            # a moving wall: the inhomogeneous ghost part is nonzero
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(3 * case.N)
+    v = rng.standard_normal(3 * case.N)
+    U = case.faces(u)
+    nut = np.abs(rng.standard_normal(case.N)) * 0.01
+    L0 = case.momentum_operator(np.zeros(3 * case.N), U, nut)
+    assert np.abs(L0).max() > 1e-3
+    Lu = case.momentum_operator(u, U, nut)
+    Lh = case.momentum_operator(u, U, nut, hom=True)
+    assert np.allclose(Lu - L0, Lh, rtol=0, atol=1e-12)
+    Lhv = case.momentum_operator(v, U, nut, hom=True)
+    Lhs = case.momentum_operator(2.0 * u - 3.0 * v, U, nut, hom=True)
+    assert np.allclose(Lhs, 2.0 * Lh - 3.0 * Lhv, rtol=0, atol=1e-11)
+
+
+def test_crank_nicolson_solves_its_system_with_a_body():
+    """u* - u^n = dt (L(u*) + L(u^n)) / 2 holds to the solve tolerance with cut links and an inflow."""
+    case = oracle.Case(14, 10, 9, nu=0.03, dt=0.3, bc=(1, 2, 3, 3, 4, 3), u_in=(1.0, 0.0, 0.0), quick=0.1,
+                       integrator=1)
+    case.set_geometry(W.icosphere(2, 2.6, (6.3, 5.1, 4.4)))
+    rng = np.random.default_rng(6)
+    u = np.concatenate([np.ones(case.N), np.zeros(2 * case.N)]) + 0.1 * rng.standard_normal(3 * case.N)
+    U = case.faces(u)
+    nut = case.csm(u)
+    H, us, it = case.predict_cn(u, U, nut, tol=1e-13, maxit=300)
+    assert it > 0
+    assert np.allclose(H, case.momentum_operator(u, U, nut), rtol=0, atol=0)
+    lhs = (us - u) / case.pr.dt
+    rhs = 0.5 * (case.momentum_operator(us, U, nut) + H)
+    assert np.linalg.norm(lhs - rhs) <= 1e-10 * np.linalg.norm(H)
+
+
+def test_crank_nicolson_uniform_flow_and_momentum():
+    n = 8
+    case = oracle.Case(n, n, n, nu=0.05, dt=0.3, bc=PER, quick=0.1, integrator=1)
+    u = np.concatenate([np.full(n ** 3, 0.3), np.full(n ** 3, -0.2), np.full(n ** 3, 0.1)])
+    H, us, it = case.predict_cn(u, case.faces(u), case.csm(u))
+    assert it == 0 and np.array_equal(us, u)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(3 * n ** 3)
+    H, us, it = case.predict_cn(u, case.faces(u), case.csm(u), tol=1e-13)
+    assert it > 0
+    d = (us - u).reshape(3, -1).sum(1)
+    assert np.all(np.abs(d) < 1e-11 * np.abs(us - u).sum())
+
+
+@pytest.mark.slow
+def test_crank_nicolson_step_converges_in_time():
+    """Taylor-Green vortex on a fixed 32x32 grid with Crank-Nicolson steps: halving dt halves the
+    difference to a dt/8 run.  The predictor alone is second order (the Fourier pin above), but the
+    step corrects with p^{n+1} only (Eq. correction, no pressure in the predictor) and advects with
+    U^n, so the whole step is first order in time."""
+    n, re, T = 32, 50.0, 0.4
+    u0, _, dx = W.taylor_green(n, 0.0, re)
+    sols = {}
+    for dt in (0.1, 0.05, 0.0125):
+        case = oracle.Case(n, n, 1, dx, 1.0 / re, dt, PER, csm_on=0, forcing_on=0, integrator=1,
+                           mom_tol=1e-13)
+        st = case.initial_state(u0)
+        for _ in range(int(round(T / dt))):
+            case.step(st, tol=1e-13)
+        sols[dt] = st["u"].copy()
+    e1 = np.linalg.norm(sols[0.1] - sols[0.0125])
+    e2 = np.linalg.norm(sols[0.05] - sols[0.0125])
+    ratio = e1 / e2
+    assert 1.8 < ratio < 2.6, ratio
+
+
+# --------------------------------------------------------------------------------------------------
+# Surface pressure and the thin-plate filter (Eq. force, Eq. force_filter)
+
+def _square(z, lo=3.1, hi=12.9):
+    a, b, c, d = (lo, lo, z), (hi, lo, z), (hi, hi, z), (lo, hi, z)
+    return np.array([[a, b, c], [a, c, d]], np.float32)
+
+
+def test_filter_cancels_the_inner_faces_of_a_thin_plate():
+    """Two parallel squares 0.1 cells apart (a plate thinner than a cell): without the filter both
+    squares see both sides and the force doubles; with it the inner faces are cancelled and the pair
+    carries the force of one square."""
+    n = 16
+    case = oracle.Case(n, n, n)
+    x = centres(n)
+    Z = np.meshgrid(x, x, x, indexing="ij")[0].reshape(-1)
+    p = 2.0 + 0.5 * Z + np.where(Z > 10.25, 1.5, 0.0)      # a jump across the plate
+    one = _square(10.2)
+    two = np.concatenate([one, _square(10.3)])
+    ps1, F1 = case.surface_pressure(one, p, zfilter=True)
+    ps0, F0 = case.surface_pressure(one, p, zfilter=False)
+    assert np.array_equal(ps1, ps0) and np.array_equal(F1, F0)          # nothing to hide behind
+    assert F1[3] == 4 and abs(F1[2]) > 1.0
+    ps2, F2 = case.surface_pressure(two, p, zfilter=True)
+    assert np.all(np.isnan(ps2[:2, 0])) and np.all(np.isnan(ps2[2:, 1]))  # inner faces cancelled
+    assert np.allclose(ps2[:2, 1], ps1[:, 1]) and not np.any(np.isnan(ps2[2:, 0]))
+    assert F2[3] == 4
+    assert np.allclose(F2[:3], F1[:3], rtol=0.0, atol=1e-12 * abs(F1[2]) + 0.02 * abs(F1[2]))
+    _, F2n = case.surface_pressure(two, p, zfilter=False)
+    assert F2n[3] == 8
+    assert F2n[2] == pytest.approx(2.0 * F1[2], rel=0.03)
+
+
+def test_filter_on_a_double_skin_sphere_gives_archimedes_once():
+    """A closed sphere wrapped in a second skin 0.1 cells outside (the frame-skin case): with p = x
+    outside and 0 inside, the filtered force is close to -V e_x of one body, the unfiltered one about
+    twice.  Cell centres that happen to lie inside the 0.1-cell gap still count for both skins (the
+    filter cancels only where no point lies between them), hence the looser bound."""
+    n = 24
+    R = 6.2
+    c = (12.1, 11.9, 12.05)
+    inner = W.icosphere(3, R, c)
+    outer = W.icosphere(3, R + 0.1, c)
+    case = oracle.Case(n, n, n)
+    x = centres(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    inside = ((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2 < (R + 0.05) ** 2).reshape(-1)
+    p = np.where(inside, 0.0, X.reshape(-1))
+    V = 4.0 / 3.0 * np.pi * R ** 3
+    _, Fs = case.surface_pressure(inner, p, zfilter=True)
+    assert Fs[0] == pytest.approx(-V, rel=0.08)
+    psf, Ff = case.surface_pressure(np.concatenate([inner, outer]), p, zfilter=True)
+    assert Ff[0] == pytest.approx(-V, rel=0.15)
+    nt = len(inner)
+    assert np.isnan(psf[:nt, 0]).mean() > 0.6 and np.isnan(psf[nt:, 1]).mean() > 0.6
+    assert not np.isnan(psf[:nt, 1]).any() and not np.isnan(psf[nt:, 0]).any()
+    _, Fn = case.surface_pressure(np.concatenate([inner, outer]), p, zfilter=False)
+    assert Fn[0] == pytest.approx(-2.0 * V, rel=0.12)
+
+
+def test_surface_pressure_uniform_and_matches_forces_on_a_clean_body():
+    n = 24
+    R = 6.2
+    c = (12.1, 11.9, 12.05)
+    tri = W.icosphere(3, R, c)
+    case = oracle.Case(n, n, n)
+    ps, F = case.surface_pressure(tri, np.full(n ** 3, 3.0), zfilter=True)
+    ok = ~np.isnan(ps)
+    assert ok.all() and np.allclose(ps, 3.0, rtol=1e-15, atol=0)
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(n ** 3)
+    ps, F = case.surface_pressure(tri, p, zfilter=False)
+    both = ~np.isnan(ps).any(1)
+    ref = case.forces(tri, p)
+    if both.all():
+        assert np.allclose(F[:3], ref[:3], rtol=1e-12, atol=1e-12)

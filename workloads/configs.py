@@ -38,6 +38,7 @@ class Config:
     seed: int = 0
     a_ref: float = 1.0
     quick: float = 0.0
+    integrator: int = 0          # 0 Adams-Bashforth 2, 1 Crank-Nicolson
     note: str = ""
 
     @property
