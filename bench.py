@@ -1,9 +1,11 @@
 """Throughput of the immersed-boundary LES step on one GB300 (or N independent replicas).
 
-A step is one fractional time step of the whole hot path (CSM eddy viscosity, AB2 predictor, IB
-forcing, face velocities, RHS, pressure solve to ||b - A p|| / ||b|| <= 1e-6, correction) on the dirty
-sphere workload: 256 x 128 x 128 cells (4.19 M), a 40.6k-triangle dirty icosphere soup, FP32 stencils
-with FP64 iterative refinement of the pressure.  Metric: Mcell-steps/s = cells * steps / seconds.
+A step is one fractional time step of the whole hot path (CSM eddy viscosity, Crank-Nicolson predictor
+with 10 % QUICK and its momentum BiCGStab, IB forcing, face velocities, RHS, pressure solve to
+||b - A p|| / ||b|| <= 1e-6, correction) on the dirty sphere workload: 256 x 128 x 128 cells (4.19 M),
+a 40.6k-triangle dirty icosphere soup, FP32 stencils with FP64 iterative refinement of the pressure.
+The default warm-up of 400 steps puts the timed window at steps 401-500 of the run.
+Metric: Mcell-steps/s = cells * steps / seconds.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,15 +32,16 @@ WORKLOAD = "dirty_sphere_256x128x128"
 METRIC = "Mcell-steps/s at Poisson rel. residual 1e-6, learned+mixed vs plain, %HBM roof"
 UNIT = "Mcell-steps/s"
 FALLBACK_HBM = 6800.0
-# CG iterations per step the oracle is charged in its extrapolated step (the GPU's measured mean on
-# this workload, timed steps after 5 warm-up steps; see the design notes)
-I_REF_DEFAULT = 40
+# CG iterations per step the oracle is charged in its extrapolated step (about the GPU's measured
+# mean of multigrid-preconditioned CG on this workload)
+I_REF_DEFAULT = 20
 
 # algorithmic bytes per cell of each timed kernel group (s = bytes of a working-precision value)
-def bytes_per_cell(s):
+def bytes_per_cell(s, integrator="cn"):
     return {
         "csm": 4 * s + 1,                 # u (3) + flags -> nu_t
-        "predict": 16 * s + 1,            # u, U, nu_t, Hprev, flags -> H, u*
+        # AB2: u, U, nu_t, Hprev, flags -> H, u*;  CN: u, U, nu_t, flags -> H, r, r_hat, delta
+        "predict": (16 * s + 1) if integrator == "ab2" else (19 * s + 1),
         "faces": 6 * s + 1,               # u*, flags -> U*
         "rhs": 3 * s + 8,                 # U* -> b (fp64)
         "residual": 8 + 8 + 1 + s,        # b, x (fp64), flags -> r
@@ -161,22 +164,26 @@ def barrier(world):
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, on a bounded sample of the same workload
 
-def oracle_sample(cfg, iters_per_step, n_iter_sample=5, planes=8):
+def oracle_sample(cfg, iters_per_step, n_iter_sample=5, planes=8, integrator="cn", quick=0.1, mom_tol=1e-6):
     """Time the FP64 oracle on a z-slab of the workload (the `planes` planes through the body's centre,
-    same soup, same per-cell work) -- one pass of every non-Poisson operator plus n_iter_sample CG
-    iterations -- and scale to one full-size step: t = (N / N_slab) * (t_ops + I * t_iter)."""
+    same soup, same per-cell work) -- one pass of every non-Poisson operator (the Crank-Nicolson
+    predictor with its momentum BiCGStab, or the AB2 predictor) plus n_iter_sample CG iterations -- and
+    scale to one full-size step: t = (N / N_slab) * (t_ops + I * t_iter)."""
     import oracle
     k0 = cfg.nz // 2 - planes // 2
     tri = cfg.soup().copy()
     tri[..., 2] -= k0
     case = oracle.Case(cfg.nx, cfg.ny, planes, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
-                       cfg.forcing_on, cfg.deadend_on)
+                       cfg.forcing_on, cfg.deadend_on, quick)
     case.set_geometry(tri)
     u = W.initial_fields(W.Config("slab", cfg.nx, cfg.ny, planes, 0, 0, 0, 0, 0, cfg.bc, seed=cfg.seed)).reshape(-1)
     U = case.faces(u)
     t0 = time.perf_counter()
     nut = case.csm(u)
-    H, us = case.predict(u, U, nut, np.zeros_like(u), True)
+    if integrator == "cn":
+        H, us, mom_it = case.predict_cn(u, U, nut, tol=mom_tol)
+    else:
+        H, us = case.predict(u, U, nut, np.zeros_like(u), True)
     us2, _ = case.forcing(us)
     Us = case.faces(us2)
     b = case.rhs(Us)
@@ -189,9 +196,11 @@ def oracle_sample(cfg, iters_per_step, n_iter_sample=5, planes=8):
     t_iter = (t2 - t1) / max(st.iters, 1)
     scale = cfg.ncell / case.N
     t_step = scale * (t_ops + iters_per_step * t_iter)
-    sample = ("oracle (FP64, 1 thread) on the %dx%dx%d slab through the body centre: one pass of csm, predict, "
-              "forcing, faces, rhs, correct plus %d CG iterations; full step = (N/N_slab) * (t_ops + I * t_iter) "
-              "with I = %.1f CG iterations per step" % (cfg.nx, cfg.ny, planes, st.iters, iters_per_step))
+    sample = ("oracle (FP64, 1 thread) on the %dx%dx%d slab through the body centre: one pass of csm, %s "
+              "predictor, forcing, faces, rhs, correct plus %d CG iterations; full step = (N/N_slab) * "
+              "(t_ops + I * t_iter) with I = %.1f CG iterations per step"
+              % (cfg.nx, cfg.ny, planes, "Crank-Nicolson (momentum BiCGStab to %g)" % mom_tol if integrator == "cn"
+                 else "AB2", st.iters, iters_per_step))
     return {"t_step_s": t_step, "t_ops_s": t_ops * scale, "t_iter_s": t_iter * scale, "sample": sample,
             "wall_s": t3 - t0}
 
@@ -202,17 +211,23 @@ def run_reference(args):
         return
     cfg = W.get_config(args.workload)
     I = float(os.environ.get("IBM_REF_ITERS", I_REF_DEFAULT))
-    for _ in range(args.warmup):
-        oracle_sample(cfg, I)
+    kw = dict(integrator=args.integrator, quick=args.quick)
+    # The oracle has nothing to warm up; one sample on an 8-plane slab stands for the W warm-up steps
+    # and sizes the K timed samples so that the whole run stays within about two minutes.
+    first = oracle_sample(cfg, I, planes=8, **kw)
+    budget_s = 120.0
+    planes = int(max(2, min(8, 8 * (budget_s / max(args.steps, 1)) / max(first["wall_s"], 1e-3))))
     times = []
     for _ in range(args.steps):
-        times.append(oracle_sample(cfg, I))
+        times.append(oracle_sample(cfg, I, planes=planes, **kw))
     t_step = float(np.mean([t["t_step_s"] for t in times]))
     value = cfg.ncell / t_step / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": cfg.ncell},
+            "config": {"workload": args.workload, "cells": cfg.ncell,
+                       "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
+                       "quick": args.quick, "slab_planes": planes},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": times[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -354,9 +369,11 @@ def run_ours(args):
     g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
     geo = L.Geometry(g, torch.from_numpy(tri).cuda(), deadend_on=cfg.deadend_on)
     precond = L.MULTIGRID if args.precond == "mg" else L.NO_PRECOND
+    integ = L.CRANK_NICOLSON if args.integrator == "cn" else L.ADAMS_BASHFORTH
     solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=cfg.precision, solver=L.CG, tol=cfg.tol,
                       max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
-                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond)
+                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond,
+                      quick=args.quick, integrator=integ)
     st = solver.fields(W.initial_fields(cfg))
     for _ in range(args.warmup):
         solver.step(st)
@@ -368,7 +385,7 @@ def run_ours(args):
     gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(local)
 
     # ---- timed region: K steps, inputs resident in HBM, the library's fast path (CUDA graphs on)
-    iters, outers, relres = [], [], []
+    iters, outers, relres, moms = [], [], [], []
     solver.profile(0)
     n_launch0 = solver.kernel_launches()
     barrier(world)
@@ -380,6 +397,7 @@ def run_ours(args):
             iters.append(s.iters)
             outers.append(s.outer)
             relres.append(s.relres)
+            moms.append(s.mom_iters)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -428,9 +446,16 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel group
     s_bytes = 8 if cfg.precision == L.FP64 else 4
-    bpc = bytes_per_cell(s_bytes)
+    bpc = bytes_per_cell(s_bytes, args.integrator)
     timed = {k: v for k, v in prof.items() if v[1] > 0 and k in bpc}
     everything = {k: v for k, v in prof.items() if v[1] > 0}
+    M = float(np.mean(moms))
+    if args.integrator == "cn" and prof["momentum"][1] > 0:
+        # the momentum BiCGStab as one launch per step: M iterations of p update (r, p, v -> p),
+        # two operator passes (input, U, nu_t, flags -> output, one dot operand) and s update
+        # (r, v -> s), x/r update (x, p, s, t, r_hat -> x, r): (68 s + 2) bytes per cell per iteration
+        bpc["momentum"] = M * (68 * s_bytes + 2)
+        timed["momentum"] = (prof["momentum"][0], args.steps)
     dom = max(timed, key=lambda k: timed[k][0])
     avg_ms = timed[dom][0] / timed[dom][1]
     algo_bytes = bpc[dom] * N
@@ -444,14 +469,18 @@ def run_ours(args):
     line = None
     if rank == 0:
         I = float(np.mean(iters))
-        cpu = oracle_sample(cfg, I) if not args.no_cpu_baseline else None
+        cpu = oracle_sample(cfg, I, integrator=args.integrator, quick=args.quick) if not args.no_cpu_baseline else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "cells": N, "grid": [cfg.nx, cfg.ny, cfg.nz],
                        "triangles": int(len(tri)), "precision": "fp32 stencils and cg, fp64 residual refinement",
-                       "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol, "parallelism": "replicas" if world > 1 else "single",
+                       "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol,
+                       "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
+                       "quick": args.quick, "momentum_bicgstab_iters_per_step": M,
+                       "timed_steps": [args.warmup + 1, args.warmup + args.steps],
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.4 GB of state per step vs 126 MB L2)",
                        "inner_iters_per_step": I, "refinements_per_step": float(np.mean(outers)),
                        "max_relres": float(np.max(relres))},
@@ -481,12 +510,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=400)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--precond", default="mg", choices=["mg", "none"])
+    ap.add_argument("--integrator", default="cn", choices=["cn", "ab2"],
+                    help="Crank-Nicolson (the paper's production integrator) or Adams-Bashforth 2")
+    ap.add_argument("--quick", type=float, default=0.1, help="QUICK fraction of the advected face value")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -89,8 +89,8 @@ typedef struct {
     double relres;       /* ||b - A p|| / ||b|| at exit, computed in FP64 */
     double bnorm;        /* ||b||_2 */
     double fsum[3];      /* momentum added by the IB forcing this step: sum of du * dx^3 */
-    double relres0;      /* with a learned guess attached: initial ||b - A p^n|| / ||b|| (else -1) */
-    double relres_guess; /* with a learned guess attached: initial residual of the guess (else -1) */
+    double relres0;      /* with a learned guess attached: initial ||b - A p^n|| / ||b|| (else -1), in FP32 */
+    double relres_guess; /* with a learned guess attached: the same for the guess (else -1), in FP32 */
     int32_t mom_iters;   /* Crank-Nicolson: momentum BiCGStab iterations of the step (0 for AB2) */
     int32_t reserved;
 } les_stats;

@@ -123,6 +123,7 @@ static void free_state(les_state* S) {
     cudaFree(S->x_guess);
     cudaFree(S->two_res);
     cudaFree(S->c.general);
+    cudaFree(S->c.fastmask);
     if (S->c.cn) {
         CNWork* w = S->c.cn;
         cudaFree(w->r); cudaFree(w->rh); cudaFree(w->p); cudaFree(w->v); cudaFree(w->sv); cudaFree(w->tv);
@@ -205,6 +206,9 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     c.D.sz = (long long)g->nx * g->ny;
     c.D.N = (long long)g->nx * g->ny * g->nz;
     c.D.dx = g->dx;
+    c.D.idx = 1.0 / g->dx;
+    c.D.fdx = (float)g->dx;
+    c.D.fidx = (float)(1.0 / g->dx);
     for (int f = 0; f < 6; ++f) c.D.bc[f] = p->bc[f];
     for (int a = 0; a < 3; ++a) c.D.u_in[a] = p->u_in[a];
     if (geom) {
@@ -221,7 +225,6 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     c.dt = p->dt;
     c.quick = p->quick;
     c.integrator = p->integrator;
-    c.flux_margin = p->quick > 0.0 ? 2 : 1;
     c.csm_on = p->csm_on;
     c.forcing_on = p->forcing_on;
     c.deadend_on = geom ? ibm_geom_deadend(geom) : 0;
@@ -266,7 +269,8 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     memset(S->hfs, 0, 8 * sizeof(double));
     S->c.nlaunch = &S->nlaunch;
     {
-        int rc1 = build_general_list(S->c, 0);
+        int rc1 = flux_kernels_setup();
+        if (!rc1) rc1 = build_general_list(S->c, 0);
         if (rc1) {
             free_state(S);
             return rc1;

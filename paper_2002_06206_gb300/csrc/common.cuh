@@ -28,15 +28,27 @@ struct Dom {
     long long sz;      // nx * ny
     long long N;
     double dx;
+    double idx;                // 1 / dx
+    float fdx, fidx;           // dx, 1 / dx rounded to FP32 (FP32 kernels do no FP64 arithmetic per cell)
     int bc[6];
     double u_in[3];
     const uint8_t* flags;      // may be null: no body
     const int32_t* cellrec;    // first record of each Omega_inc cell, -1 elsewhere
     const LinkRec* rec;
     int hom;                   // 1: ghost values without wall and inflow velocities (linear part)
+    const uint8_t* fast;       // momentum flux: 1 where the tiled fast path applies (may be null)
 };
 
 __device__ __forceinline__ int link_bit(int a, int s) { return 2 * a + (s > 0); }
+
+// dx and 1/dx in the working precision (set on the host; GB300's FP64 rate is a small fraction of its
+// FP32 rate, so a per-cell FP64 division would dominate an FP32 stencil).
+template <class T> __device__ __forceinline__ T dom_dx(const Dom& D);
+template <> __device__ __forceinline__ float dom_dx<float>(const Dom& D) { return D.fdx; }
+template <> __device__ __forceinline__ double dom_dx<double>(const Dom& D) { return D.dx; }
+template <class T> __device__ __forceinline__ T dom_idx(const Dom& D);
+template <> __device__ __forceinline__ float dom_idx<float>(const Dom& D) { return D.fidx; }
+template <> __device__ __forceinline__ double dom_idx<double>(const Dom& D) { return D.idx; }
 
 __device__ __forceinline__ const LinkRec& link_record(const Dom& D, long long P, unsigned fl, int bit) {
     return D.rec[D.cellrec[P] + __popc(fl & 63u & ((1u << bit) - 1u))];
@@ -129,11 +141,31 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
-// Deterministic grid-wide reduction of `nv` doubles per block: every block stores its partials, the
-// last block to arrive sums them in block order and calls fin(totals).  `counter` must be zero on
-// entry and is left zero.
-template <int NV, class Fin>
-__device__ __forceinline__ void grid_reduce(double (&v)[NV], double* __restrict__ partials,
+// Block-wide sum of per-thread FP32 partials, in FP32 (GB300 runs FP64 at a small fraction of its
+// FP32 rate, and an FP64 shuffle tree in every block of a one-cell-per-thread launch costs more than
+// the kernel's own arithmetic); the block total is widened to FP64 for the grid stage.
+__device__ __forceinline__ double block_sum(float v, double* sh) {
+    float* shf = reinterpret_cast<float*>(sh);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int w = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
+    if ((tid & 31) == 0) shf[w] = v;
+    __syncthreads();
+    v = 0.f;
+    if (tid < 32) {
+        v = tid < nw ? shf[tid] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return (double)v;
+}
+
+// Deterministic grid-wide reduction of `nv` values per block (double, or float summed in FP32 within
+// the block): every block stores its partials in FP64, the last block to arrive sums them in block
+// order and calls fin(totals).  `counter` must be zero on entry and is left zero.
+template <int NV, class A, class Fin>
+__device__ __forceinline__ void grid_reduce(A (&v)[NV], double* __restrict__ partials,
                                             unsigned int* counter, Fin fin) {
     __shared__ double sh[32];
     __shared__ bool last;

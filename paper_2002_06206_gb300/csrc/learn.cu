@@ -1,11 +1,11 @@
 // learn.cu -- learned initial guess of the pressure Poisson solve: a small 3-D convolutional network
 // (three 3x3x3 convolutions, 8 -> 8 -> 8 -> 1 channels, ReLU between) on the solver's grid that
-// predicts the pressure change p^{n+1} - p^n from the right-hand side, the last pressure change and
-// the solid mask.  Activations and gradients are stored in BF16, channel-last (8 channels = 16 bytes
-// per cell); the convolutions run as implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation): M = 16 consecutive cells of a row, N = 8 channels, K = 27 taps x 8
-// channels (padded to 224).  The weight gradient is a reduction over all cells, done on the CUDA cores
-// in FP32 with per-block partial sums reduced in a fixed order.
+// predicts how far p^{n+1} departs from the linear extrapolation 2 p^n - p^{n-1}, from the right-hand
+// side, the last pressure change and the solid mask.  Activations and gradients are stored in BF16,
+// channel-last (8 channels = 16 bytes per cell); the convolutions run as implicit GEMMs on the tensor
+// cores (ldmatrix + mma.sync m16n8k16, BF16 operands, FP32 accumulation): M = 16 consecutive cells of
+// a row, N = 8 channels, K = 27 taps x 8 channels (padded to 224).  The weight gradient is a reduction
+// over all cells, done on the CUDA cores in FP32 with per-block partial sums reduced in a fixed order.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -60,18 +60,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// The 32-bit word holding channels (c2, c2+1) of cell (i, j, k) + tap offset, 0 outside the grid.
-__device__ __forceinline__ uint32_t act_pair(const __nv_bfloat16* __restrict__ a, int nx, int ny, int nz, int i, int j,
-                                             int k, int t, int c2, int sgn) {
-    if (t >= NN_TAPS) return 0u;
-    int dz, dy, dx;
-    tap_off(t, dz, dy, dx);
-    const int ii = i + sgn * dx, jj = j + sgn * dy, kk = k + sgn * dz;
-    if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) return 0u;
-    const long long c = ii + (long long)nx * (jj + (long long)ny * kk);
-    return *reinterpret_cast<const uint32_t*>(a + c * NN_C + c2);
-}
-
 __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -80,60 +68,106 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], const 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Convolution of a channel-last BF16 field with 27 taps on the tensor cores.  One warp computes 16
-// consecutive cells of a row.  sgn = +1: forward (input at c + off); sgn = -1: input gradient (input
-// at c - off, transposed weights).  mode 0: store BF16 relu(acc + bias); mode 1: store FP32 channel 0
-// of acc + bias; mode 2: store BF16 acc masked by (mask > 0) at the output cell (ReLU derivative).
-__global__ void __launch_bounds__(256) k_nn_conv(int nx, int ny, int nz, const __nv_bfloat16* __restrict__ in,
-                                                 const uint32_t* __restrict__ frag, const float* __restrict__ bias,
-                                                 int sgn, int mode, __nv_bfloat16* __restrict__ outb,
-                                                 float* __restrict__ outf, const __nv_bfloat16* __restrict__ mask) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const int segs = (nx + 15) / 16;
-    const long long nwarps = (long long)segs * ny * nz;
-    if (warp >= nwarps) return;
-    const int seg = (int)(warp % segs);
-    const int j = (int)((warp / segs) % ny);
-    const int k = (int)(warp / ((long long)segs * ny));
+// Convolution of a channel-last BF16 field with 27 taps on the tensor cores (implicit GEMM, K = 27
+// taps x 8 channels padded to 224).  sgn = +1: forward (input at c + off); sgn = -1: input gradient
+// (input at c - off, transposed weights).  mode 0: store BF16 relu(acc + bias); mode 1: store FP32
+// channel 0 of acc + bias; mode 2: store BF16 acc masked by (mask > 0) at the output cell (ReLU
+// derivative).  The input is staged in shared memory.  A block owns a 32 x 4 (x, y) tile
+// of output cells and walks NC_KZ planes; the input planes k - 1, k, k + 1 over the tile plus a one-cell
+// halo sit in a three-plane ring (16 bytes per cell, zero outside the grid).  Warp w computes the
+// 16 cells (w % 2) * 16 .. + 15 of row w / 2: for each k-step (two taps x 8 channels) one
+// ldmatrix.x4 gathers the A fragment straight from the ring -- each lane names one 16-byte row, the
+// input cell of its (cell, tap) -- and one mma.sync accumulates it.
+#define NC_TX 32
+#define NC_TY 4
+#define NC_KZ 8
+#define NC_SX (NC_TX + 2)
+#define NC_SY (NC_TY + 2)
+#define NC_PL (NC_SX * NC_SY)
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__global__ void __launch_bounds__(256) k_nn_conv_tile(int nx, int ny, int nz, const __nv_bfloat16* __restrict__ in,
+                                                      const uint32_t* __restrict__ frag, const float* __restrict__ bias,
+                                                      int sgn, int mode, __nv_bfloat16* __restrict__ outb,
+                                                      float* __restrict__ outf, const __nv_bfloat16* __restrict__ mask) {
+    __shared__ __align__(16) uint4 ring[3 * NC_PL + 1];          // + one zero row for the padding tap
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int x0 = blockIdx.x * NC_TX, y0 = blockIdx.y * NC_TY, z0 = blockIdx.z * NC_KZ;
+    const int z1 = z0 + NC_KZ < nz ? z0 + NC_KZ : nz;
+    if (tid == 0) ring[3 * NC_PL] = make_uint4(0u, 0u, 0u, 0u);
+    auto load_plane = [&](int kk) {
+        uint4* dst = ring + ((kk % 3) + 3) % 3 * NC_PL;
+        for (int e = tid; e < NC_PL; e += 256) {
+            const int gx = x0 + e % NC_SX - 1, gy = y0 + e / NC_SX - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (kk >= 0 && kk < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                v = *reinterpret_cast<const uint4*>(in + (gx + (long long)nx * (gy + (long long)ny * kk)) * NN_C);
+            dst[e] = v;
+        }
+    };
     const int g = lane >> 2, q = lane & 3;
-    const int i_lo = seg * 16 + g, i_hi = i_lo + 8;
     uint32_t bf[NN_KSTEPS][2];
 #pragma unroll
     for (int s = 0; s < NN_KSTEPS; ++s) {
         bf[s][0] = frag[(s * 32 + lane) * 2 + 0];
         bf[s][1] = frag[(s * 32 + lane) * 2 + 1];
     }
-    float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int s = 0; s < NN_KSTEPS; ++s) {
-        uint32_t a[4];
-        a[0] = i_lo < nx ? act_pair(in, nx, ny, nz, i_lo, j, k, 2 * s, 2 * q, sgn) : 0u;
-        a[1] = i_hi < nx ? act_pair(in, nx, ny, nz, i_hi, j, k, 2 * s, 2 * q, sgn) : 0u;
-        a[2] = i_lo < nx ? act_pair(in, nx, ny, nz, i_lo, j, k, 2 * s + 1, 2 * q, sgn) : 0u;
-        a[3] = i_hi < nx ? act_pair(in, nx, ny, nz, i_hi, j, k, 2 * s + 1, 2 * q, sgn) : 0u;
-        mma_bf16(d, a, bf[s]);
-    }
-    const long long row = (long long)nx * (j + (long long)ny * k);
     const float b0 = bias ? bias[2 * q] : 0.f, b1 = bias ? bias[2 * q + 1] : 0.f;
+    // this lane's ldmatrix row: matrix mj = lane / 8 (cells +8 for odd mj, tap +1 for mj >= 2), row lane % 8
+    const int mj = lane >> 3, mr = lane & 7;
+    const int cx = (w & 1) * 16 + ((mj & 1) ? 8 : 0) + mr;          // tile-local output x of the row
+    const int cy = w >> 1;
+    const uint32_t ring_base = (uint32_t)__cvta_generic_to_shared(ring);
+    const uint32_t zero_row = ring_base + 3 * NC_PL * 16;
+    load_plane(z0 - 1);
+    load_plane(z0);
+    for (int k = z0; k < z1; ++k) {
+        load_plane(k + 1);
+        __syncthreads();
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = h ? i_hi : i_lo;
-        if (i >= nx) continue;
-        const long long c = row + i;
-        float v0 = d[2 * h] + b0, v1 = d[2 * h + 1] + b1;
-        if (mode == 0) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-            *reinterpret_cast<uint32_t*>(outb + c * NN_C + 2 * q) = pack_bf16(v0, v1);
-        } else if (mode == 1) {
-            if (q == 0) outf[c] = v0;
-        } else {
-            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + c * NN_C + 2 * q);
-            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-            *reinterpret_cast<uint32_t*>(outb + c * NN_C + 2 * q) = pack_bf16(v0, v1);
+        for (int s = 0; s < NN_KSTEPS; ++s) {
+            const int t = 2 * s + (mj >> 1);
+            uint32_t addr = zero_row;
+            if (t < NN_TAPS) {
+                int dz, dy, dx;
+                tap_off(t, dz, dy, dx);
+                const int sl = (((k + sgn * dz) % 3) + 3) % 3;
+                addr = ring_base + (uint32_t)((sl * NC_PL + (cy + sgn * dy + 1) * NC_SX + (cx + sgn * dx + 1)) * 16);
+            }
+            uint32_t a[4];
+            ldsm_x4(a, addr);
+            // ldmatrix returns the matrices in lane order: 0 cells 0-7 tap 2s, 1 cells 8-15 tap 2s,
+            // 2 cells 0-7 tap 2s+1, 3 cells 8-15 tap 2s+1 -- the a0..a3 order of mma's A fragment
+            mma_bf16(d, a, bf[s]);
         }
+        const int j = y0 + cy;
+        const long long row = (long long)nx * (j + (long long)ny * k);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = x0 + (w & 1) * 16 + g + 8 * h;
+            if (i >= nx || j >= ny) continue;
+            const long long c = row + i;
+            float v0 = d[2 * h] + b0, v1 = d[2 * h + 1] + b1;
+            if (mode == 0) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+                *reinterpret_cast<uint32_t*>(outb + c * NN_C + 2 * q) = pack_bf16(v0, v1);
+            } else if (mode == 1) {
+                if (q == 0) outf[c] = v0;
+            } else {
+                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + c * NN_C + 2 * q);
+                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                *reinterpret_cast<uint32_t*>(outb + c * NN_C + 2 * q) = pack_bf16(v0, v1);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -403,10 +437,10 @@ extern "C" int ibm_net_get_grads(const ibm_net* n, float* h_grads) {
 
 static void conv(const ibm_net* n, int nx, int ny, int nz, const __nv_bfloat16* in, int l, int sgn, int mode,
                  __nv_bfloat16* outb, float* outf, const __nv_bfloat16* mask, cudaStream_t s) {
-    const long long warps = (long long)((nx + 15) / 16) * ny * nz;
-    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
-    k_nn_conv<<<blocks, 256, 0, s>>>(nx, ny, nz, in, sgn > 0 ? n->frag_fwd[l] : n->frag_bwd[l],
-                                     sgn > 0 ? n->master + offset_b(l) : nullptr, sgn, mode, outb, outf, mask);
+    const dim3 grid((unsigned)((nx + NC_TX - 1) / NC_TX), (unsigned)((ny + NC_TY - 1) / NC_TY),
+                    (unsigned)((nz + NC_KZ - 1) / NC_KZ));
+    k_nn_conv_tile<<<grid, 256, 0, s>>>(nx, ny, nz, in, sgn > 0 ? n->frag_fwd[l] : n->frag_bwd[l],
+                                        sgn > 0 ? n->master + offset_b(l) : nullptr, sgn, mode, outb, outf, mask);
 }
 
 static int net_forward(ibm_net* n, const ibm_grid* g, cudaStream_t s) {

@@ -33,7 +33,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_csm(Dom D, const T* __restrict__ u, T* __restrict__ nut) {
     const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const T inv2dx = (T)(0.5 / D.dx), delta2 = (T)(D.dx * D.dx);
+    const T inv2dx = (T)0.5 * dom_idx<T>(D), delta2 = dom_dx<T>(D) * dom_dx<T>(D);
     const long long P = i + (long long)D.sy * j + D.sz * k;
     const unsigned fl = flags_at(D, P);
     const int x[3] = {i, j, k};
@@ -94,83 +94,215 @@ __device__ __forceinline__ T face_adv(const Dom& D, const T* __restrict__ u, int
 
 // L(u) of a cell per unit volume: flux-form advection with the face velocity U (central value
 // blended with QUICK), diffusion with nu + nu_t, the transpose part of the SGS stress divergence.
-// flux_general applies the ghost and boundary rules of vel_across on every link; flux_fast is the same
-// formulas for a cell where they reduce to direct reads (fast_cell).  With D.hom set the ghost values
+// flux_general applies the ghost and boundary rules of vel_across on every link; the tiled fast path
+// evaluates the same formulas for a cell where they reduce to direct reads (fast_cell).  With D.hom set the ghost values
 // lose their wall and inflow velocities, which gives the linear part of L.
 
-// The cell and its six neighbours have no cut link and the cell lies at least mrg cells inside every
-// domain face (mrg = 2 with QUICK, whose far-upwind value is two cells away).
-__device__ __forceinline__ bool fast_cell(const Dom& D, long long P, int i, int j, int k, int mrg) {
-    if (i < mrg || i >= D.nx - mrg || j < mrg || j >= D.ny - mrg || k < mrg || k >= D.nz - mrg) return false;
+// The cell and its six neighbours (across periodic seams too) have no cut link: its flux then needs
+// only neighbour values and the domain-boundary ghosts, which the tiles below hold.
+__device__ __forceinline__ bool fast_cell(const Dom& D, long long P, int i, int j, int k) {
     if (!D.flags) return true;
     const uint8_t* f = D.flags;
-    return (f[P] | f[P - 1] | f[P + 1] | f[P - D.sy] | f[P + D.sy] | f[P - D.sz] | f[P + D.sz]) == 0;
+    unsigned m = f[P];
+    const int x[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            long long off;
+            if (nb_offset(D, a, s, x[a], off)) m |= f[P + off];
+        }
+    return (m & 63u) == 0u;
+}
+
+// Fast cells run in z-marching tiles: a block of 32 x 8 threads owns an (x, y) tile and walks FT_KZ
+// planes; u (three components) and nu_t of the planes k-2 .. k+2 over the tile plus a two-cell halo
+// sit in a five-plane ring in shared memory, so every neighbour read of the flux is a shared-memory
+// load at a fixed offset.  Halo positions across a periodic seam hold the wrapped cell; one cell
+// beyond a non-periodic domain face they hold the boundary ghost of vel_across (a function of the
+// cell across that face alone), so cells on the domain faces are fast too.  Links through a domain
+// face take the boundary forms of flux_general (near-cell nu_t and cross derivative, central advected
+// value).  Cells that are not fast_cell are skipped (the general kernel takes them).
+#define FT_X 32
+#define FT_Y 8
+#define FT_H 2
+#define FT_SX (FT_X + 2 * FT_H)
+#define FT_SY (FT_Y + 2 * FT_H)
+#define FT_PL (FT_SX * FT_SY)
+#define FT_NV 4
+#define FT_KZ 16
+#define FT_RING 6
+
+// Domain-boundary ghost of component c across face (a, s) of the cell holding v (vel_across's rules).
+template <class T>
+__device__ __forceinline__ T bc_ghost(const Dom& D, int a, int s, int c, T v) {
+    switch (D.bc[2 * a + (s > 0)]) {
+        case IBM_BC_INFLOW: return (D.hom ? (T)0 : (T)2 * (T)D.u_in[c]) - v;
+        case IBM_BC_OUTFLOW: return v;
+        case IBM_BC_SLIP: return c == a ? -v : v;
+        default: return -v;
+    }
+}
+
+template <class T, class Epi>
+__device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
+                                                const T* __restrict__ U, const T* __restrict__ nut, T nu, T gam,
+                                                Epi epi) {
+    extern __shared__ __align__(16) unsigned char ft_raw[];
+    T* sm = reinterpret_cast<T*>(ft_raw);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + FT_X * ty;
+    const T inv2dx = (T)0.5 * dom_idx<T>(D), invdx = dom_idx<T>(D);
+    auto slot = [](int kk) { return ((kk % FT_RING) + FT_RING) % FT_RING; };
+    const int n[3] = {D.nx, D.ny, D.nz};
+    const int gx = (D.nx + FT_X - 1) / FT_X, gy = (D.ny + FT_Y - 1) / FT_Y, gz = (D.nz + FT_KZ - 1) / FT_KZ;
+    const long long items = (long long)gx * gy * gz;
+    // the planes' values a thread stages: FT_PL <= 2 * 256 halo-tile positions per plane
+    T pf[2][FT_NV];
+    int x0 = 0, y0 = 0;
+    auto fetch = [&](int kk) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int e = tid + t * (FT_X * FT_Y);
+            pf[t][0] = pf[t][1] = pf[t][2] = pf[t][3] = (T)0;
+            if (e >= FT_PL) continue;
+            int g[3] = {x0 + e % FT_SX - FT_H, y0 + e / FT_SX - FT_H, kk};
+            int out = 0, oa = 0, os = 0, depth = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (g[a] >= 0 && g[a] < n[a]) continue;
+                if (D.bc[2 * a] == IBM_BC_PERIODIC) {
+                    g[a] = ((g[a] % n[a]) + n[a]) % n[a];
+                    continue;
+                }
+                ++out;
+                oa = a;
+                os = g[a] < 0 ? -1 : 1;
+                depth = g[a] < 0 ? -g[a] : g[a] - n[a] + 1;
+                g[a] = g[a] < 0 ? 0 : n[a] - 1;
+            }
+            // corners and second ghost layers are never read by a fast cell
+            if (out > 1 || depth > 1 || g[0] < 0 || g[0] >= n[0] || g[1] < 0 || g[1] >= n[1] || g[2] < 0 ||
+                g[2] >= n[2])
+                continue;
+            const long long c = g[0] + (long long)D.sy * g[1] + D.sz * g[2];
+            T v0 = u[c], v1 = u[D.N + c], v2 = u[2 * D.N + c];
+            if (out) {
+                v0 = bc_ghost(D, oa, os, 0, v0);
+                v1 = bc_ghost(D, oa, os, 1, v1);
+                v2 = bc_ghost(D, oa, os, 2, v2);
+            }
+            pf[t][0] = v0;
+            pf[t][1] = v1;
+            pf[t][2] = v2;
+            pf[t][3] = nut[c];
+        }
+    };
+    auto commit = [&](int kk) {
+        T* dst = sm + slot(kk) * (FT_NV * FT_PL);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int e = tid + t * (FT_X * FT_Y);
+            if (e >= FT_PL) continue;
+#pragma unroll
+            for (int v = 0; v < FT_NV; ++v) dst[v * FT_PL + e] = pf[t][v];
+        }
+    };
+    const int cidx = (ty + FT_H) * FT_SX + (tx + FT_H);
+    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+        x0 = (int)(item % gx) * FT_X;
+        y0 = (int)((item / gx) % gy) * FT_Y;
+        const int z0 = (int)(item / ((long long)gx * gy)) * FT_KZ;
+        const int z1 = z0 + FT_KZ < D.nz ? z0 + FT_KZ : D.nz;
+        for (int kk = z0 - 2; kk <= z0 + 2; ++kk) {
+            fetch(kk);
+            commit(kk);
+        }
+        __syncthreads();
+        const int i = x0 + tx, j = y0 + ty;
+        for (int k = z0; k < z1; ++k) {
+            // plane k + 3 is fetched while plane k is computed and lands in the ring slot that plane
+            // k - 3 left; the barrier at the end of the step publishes it
+            const bool more = k + 3 <= z1 + 1;
+            if (more) fetch(k + 3);
+        const long long P = i + (long long)D.sy * j + D.sz * k;
+        if (i < D.nx && j < D.ny && (D.fast ? D.fast[P] != 0 : fast_cell(D, P, i, j, k))) {
+            const int xc[3] = {i, j, k};
+            const T* S[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) S[d] = sm + slot(k + d - 2) * (FT_NV * FT_PL) + cidx;
+            // value of variable v at (i + dx, j + dy, k + dz)
+            auto V = [&](int v, int dx, int dy, int dz) -> T { return S[dz + 2][v * FT_PL + dy * FT_SX + dx]; };
+            const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+            const T nutP = V(3, 0, 0, 0);
+            T h[3] = {0, 0, 0};
+            T uc[3], un[3][6], GP[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uc[c] = V(c, 0, 0, 0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    un[c][2 * a] = V(c, -e[a][0], -e[a][1], -e[a][2]);
+                    un[c][2 * a + 1] = V(c, e[a][0], e[a][1], e[a][2]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int s = -1; s <= 1; s += 2) {
+                    const int lb = 2 * a + (s > 0);
+                    const T Uf = U[F.index(a, i + (a == 0 && s > 0), j + (a == 1 && s > 0), k + (a == 2 && s > 0))];
+                    const int ox = s * e[a][0], oy = s * e[a][1], oz = s * e[a][2];
+                    // a link through a non-periodic domain face
+                    const bool dom = (xc[a] + s < 0 || xc[a] + s >= n[a]) && D.bc[2 * a] != IBM_BC_PERIODIC;
+                    const T nutf = dom ? nutP : (T)0.5 * (nutP + V(3, ox, oy, oz));
+                    T GN[3] = {0, 0, 0};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (q == a) continue;
+                        GN[q] = (V(a, ox + e[q][0], oy + e[q][1], oz + e[q][2]) -
+                                 V(a, ox - e[q][0], oy - e[q][1], oz - e[q][2])) * inv2dx;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const T uP = uc[c], uN = un[c][lb];
+                        const T D1 = (uN - uP) * invdx;
+                        const T Tt = c == a ? D1 : (dom ? (T)s * GP[c][a] : (T)s * (T)0.5 * (GP[c][a] + GN[c]));
+                        T adv = (T)0.5 * (uP + uN);
+                        if (gam != (T)0 && !dom) {
+                            // far upwind: L - e_a for U >= 0 (L = P or P - e_a), R + e_a otherwise
+                            const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
+                            const int fo = Uf >= (T)0 ? (s > 0 ? -1 : -2) : (s > 0 ? 2 : 1);
+                            const T far = V(c, fo * e[a][0], fo * e[a][1], fo * e[a][2]);
+                            const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - far) / (T)8
+                                                   : ((T)6 * uR + (T)3 * uL - far) / (T)8;
+                            adv = ((T)1 - gam) * adv + gam * q;
+                        }
+                        const T conv = -(T)s * Uf * adv;
+                        h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
+                    }
+                }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[c] *= invdx;
+            epi(P, h, uc);
+        }
+            if (more) commit(k + 3);
+            __syncthreads();
+        }
+    }
 }
 
 template <class T>
-__device__ __forceinline__ void flux_fast(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
-                                          const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
-                                          int j, int k, T nu, T gam, T (&h)[3]) {
-    const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
-    const int x[3] = {i, j, k};
-    const long long o[3] = {1, (long long)D.sy, D.sz};
-    const T nutP = nut[P];
-    h[0] = h[1] = h[2] = (T)0;
-        T uc[3], un[3][6], GP[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            uc[c] = u[c * D.N + P];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                un[c][2 * a] = u[c * D.N + P - o[a]];
-                un[c][2 * a + 1] = u[c * D.N + P + o[a]];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int s = -1; s <= 1; s += 2) {
-                const int lb = 2 * a + (s > 0);
-                const T Uf = U[F.index(a, x[0] + (a == 0 && s > 0), x[1] + (a == 1 && s > 0), x[2] + (a == 2 && s > 0))];
-                const long long Nn = P + s * o[a];
-                const T nutf = (T)0.5 * (nutP + nut[Nn]);
-                T GN[3] = {0, 0, 0};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (q == a) continue;
-                    GN[q] = (u[a * D.N + Nn + o[q]] - u[a * D.N + Nn - o[q]]) * inv2dx;
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const T uP = uc[c], uN = un[c][lb];
-                    const T D1 = (uN - uP) * invdx;
-                    const T Tt = c == a ? D1 : (T)s * (T)0.5 * (GP[c][a] + GN[c]);
-                    T adv = (T)0.5 * (uP + uN);
-                    if (gam != (T)0) {
-                        // L = P (s > 0) or P - e_a (s < 0); far upwind is L - e_a or R + e_a
-                        const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
-                        const long long Lc = s > 0 ? P : Nn, Rc = s > 0 ? Nn : P;
-                        const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - u[c * D.N + Lc - o[a]]) / (T)8
-                                               : ((T)6 * uR + (T)3 * uL - u[c * D.N + Rc + o[a]]) / (T)8;
-                        adv = ((T)1 - gam) * adv + gam * q;
-                    }
-                    const T conv = -(T)s * Uf * adv;
-                    h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
-                }
-            }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) h[c] *= invdx;
-}
+size_t fast_tile_smem() { return (size_t)FT_RING * FT_NV * FT_PL * sizeof(T); }
 
 template <class T>
 __device__ __forceinline__ void flux_general(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
                                              const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
                                              int j, int k, T nu, T gam, T (&h)[3]) {
-    const T inv2dx = (T)(0.5 / D.dx), invdx = (T)(1.0 / D.dx);
+    const T inv2dx = (T)0.5 * dom_idx<T>(D), invdx = dom_idx<T>(D);
     const int n[3] = {D.nx, D.ny, D.nz};
     const unsigned fl = flags_at(D, P);
     const int x[3] = {i, j, k};
@@ -227,34 +359,35 @@ __device__ __forceinline__ void cell_coords(const Dom& D, long long P, int& i, i
     i = (int)(r - (long long)j * D.sy);
 }
 
-// Calls body(P, i, j, k) for the cells of the current thread: in the fast kernels one cell of a flat
-// (x, y) tile with one plane per block, skipped unless fast_cell (the general kernel takes it); in the
-// general kernels the entries of the list of the other cells, strided over a capped grid.
-template <bool GENERAL, class Body>
-__device__ __forceinline__ void for_flux_cells(const Dom& D, const int32_t* __restrict__ list, long long nlist,
-                                               int mrg, Body body) {
-    if (GENERAL) {
-        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nlist;
-             q += (long long)gridDim.x * blockDim.x) {
-            const long long P = list[q];
-            int i, j, k;
-            cell_coords(D, P, i, j, k);
-            body(P, i, j, k);
-        }
-        return;
+// Calls body(P, i, j, k) for the entries of the list of the cells that are not fast_cell, strided
+// over a capped grid.
+template <class Body>
+__device__ __forceinline__ void for_general_cells(const Dom& D, const int32_t* __restrict__ list, long long nlist,
+                                                  Body body) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nlist; q += (long long)gridDim.x * blockDim.x) {
+        const long long P = list[q];
+        int i, j, k;
+        cell_coords(D, P, i, j, k);
+        body(P, i, j, k);
     }
-    const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
-    if (i >= D.nx || j >= D.ny) return;
-    const long long P = i + (long long)D.sy * j + D.sz * k;
-    if (fast_cell(D, P, i, j, k, mrg)) body(P, i, j, k);
 }
 
-template <bool GENERAL, class T>
-__device__ __forceinline__ void cell_flux(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
-                                          const T* __restrict__ U, const T* __restrict__ nut, long long P, int i,
-                                          int j, int k, T nu, T gam, T (&h)[3]) {
-    if (GENERAL) flux_general(D, F, u, U, nut, P, i, j, k, nu, gam, h);
-    else flux_fast(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+// Runs epi(P, h, u_P) over the kernel's cells: z-marching shared-memory tiles of fast cells, or the
+// general list.
+template <bool GENERAL, class T, class Epi>
+__device__ __forceinline__ void flux_cells(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
+                                           const T* __restrict__ U, const T* __restrict__ nut, T nu, T gam,
+                                           const int32_t* __restrict__ list, long long nlist, Epi epi) {
+    if constexpr (GENERAL) {
+        for_general_cells(D, list, nlist, [&](long long P, int i, int j, int k) {
+            T h[3];
+            flux_general(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+            const T uc[3] = {u[P], u[D.N + P], u[2 * D.N + P]};
+            epi(P, h, uc);
+        });
+    } else {
+        fast_tile_march<T>(D, F, u, U, nut, nu, gam, epi);
+    }
 }
 
 // Momentum predictor, Adams-Bashforth 2 in time (Euler on the first step).  One thread per cell.
@@ -268,18 +401,15 @@ template <bool GENERAL, class T>
 __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_predict(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
                                                  const T* __restrict__ nut, const T* Hprev, T* H,
                                                  T* __restrict__ ustar, T nu, T dt, int first, T gam,
-                                                 const int32_t* __restrict__ list, long long nlist, int mrg) {
-    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
-        T h[3];
-        cell_flux<GENERAL>(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+                                                 const int32_t* __restrict__ list, long long nlist) {
+    flux_cells<GENERAL, T>(D, F, u, U, nut, nu, gam, list, nlist, [&](long long P, const T (&h)[3], const T (&uc)[3]) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long oc = c * D.N + P;
             const T hc = h[c];
-            const T uP = u[oc];
             const T hp = first ? (T)0 : Hprev[oc];
             H[oc] = hc;
-            ustar[oc] = first ? uP + dt * hc : uP + dt * ((T)1.5 * hc - (T)0.5 * hp);
+            ustar[oc] = first ? uc[c] + dt * hc : uc[c] + dt * ((T)1.5 * hc - (T)0.5 * hp);
         }
     });
 }
@@ -468,10 +598,10 @@ __global__ void __launch_bounds__(256) k_rhs(Dom D, FaceLayout F, const T* __res
 // Eq. correction on the cells: central pressure gradient through the link values.
 template <class T>
 __global__ void __launch_bounds__(256) k_correct_cells(Dom D, const T* __restrict__ us, const double* __restrict__ p,
-                                                       T* __restrict__ u, double dt) {
+                                                       T* __restrict__ u, T c) {
+    // c = dt / (2 dx); the FP64 pressure difference is rounded once, then scaled
     const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y, k = blockIdx.z;
     if (i >= D.nx || j >= D.ny) return;
-    const T c = (T)(dt / (2.0 * D.dx));     // the FP64 pressure difference is rounded once, then scaled
     {
         const long long P = i + (long long)D.sy * j + D.sz * k;
         const unsigned fl = flags_at(D, P);
@@ -488,7 +618,7 @@ __global__ void __launch_bounds__(256) k_correct_cells(Dom D, const T* __restric
 // Eq. correction on the faces of axis a: compact pressure difference across the face.
 template <class T>
 __global__ void k_correct_faces(Dom D, FaceLayout F, int a, const T* __restrict__ Us, const double* __restrict__ p,
-                                T* __restrict__ U, double dt) {
+                                T* __restrict__ U, T dtdx) {
     const long long nf = (long long)F.dim[a][0] * F.dim[a][1] * F.dim[a][2];
     const int na = a == 0 ? D.nx : (a == 1 ? D.ny : D.nz);
     const long long st = a == 0 ? 1 : (a == 1 ? (long long)D.sy : D.sz);
@@ -521,7 +651,7 @@ __global__ void k_correct_faces(Dom D, FaceLayout F, int a, const T* __restrict_
                 continue;
             }
         }
-        U[fi] = Us[fi] - (T)(dt / D.dx) * (T)(pr - pl);
+        U[fi] = Us[fi] - dtdx * (T)(pr - pl);
     }
 }
 
@@ -604,11 +734,9 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_begin(
                                                   const T* __restrict__ nut, T* __restrict__ H, T* __restrict__ r,
                                                   T* __restrict__ rh, T* __restrict__ x, T nu, T gam, T dt, double tol2,
                                                   int maxit, SolveScal* sc, double* partials, unsigned* counter,
-                                                  const int32_t* __restrict__ list, long long nlist, int mrg) {
+                                                  const int32_t* __restrict__ list, long long nlist) {
     T a0 = 0;
-    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
-        T h[3];
-        cell_flux<GENERAL>(D, F, u, U, nut, P, i, j, k, nu, gam, h);
+    flux_cells<GENERAL, T>(D, F, u, U, nut, nu, gam, list, nlist, [&](long long P, const T (&h)[3], const T (&uc)[3]) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long q = c * D.N + P;
@@ -620,7 +748,7 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_begin(
             a0 += b * b;
         }
     });
-    double acc[1] = {(double)a0};
+    T acc[1] = {a0};
     grid_reduce<1>(acc, partials, counter, [&](double* t) {
         if (!GENERAL) {
             sc->part[0] = t[0];
@@ -661,16 +789,14 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(
                                                   const T* __restrict__ U, const T* __restrict__ nut,
                                                   T* __restrict__ y, const T* __restrict__ w, T nu, T gam, T hdt,
                                                   int mode, SolveScal* sc, double* partials, unsigned* counter,
-                                                  const int32_t* __restrict__ list, long long nlist, int mrg) {
+                                                  const int32_t* __restrict__ list, long long nlist) {
     if (sc->done) return;
     T a0 = 0, a1 = 0;
-    for_flux_cells<GENERAL>(D, list, nlist, mrg, [&](long long P, int i, int j, int k) {
-        T h[3];
-        cell_flux<GENERAL>(D, F, xin, U, nut, P, i, j, k, nu, gam, h);
+    flux_cells<GENERAL, T>(D, F, xin, U, nut, nu, gam, list, nlist, [&](long long P, const T (&h)[3], const T (&uc)[3]) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long q = c * D.N + P;
-            const T xv = xin[q];
+            const T xv = uc[c];
             const T yv = xv - hdt * h[c];
             y[q] = yv;
             if (mode == 0) {
@@ -681,7 +807,7 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(
             }
         }
     });
-    double acc[2] = {(double)a0, (double)a1};
+    T acc[2] = {a0, a1};
     grid_reduce<2>(acc, partials, counter, [&](double* t) {
         if (!GENERAL) {
             sc->part[0] = t[0];
@@ -729,7 +855,7 @@ __global__ void __launch_bounds__(256) k_cn_xr(long long n, const T* __restrict_
         a0 += rh[q] * rv;
         a1 += rv * rv;
     }
-    double acc[2] = {(double)a0, (double)a1};
+    T acc[2] = {a0, a1};
     grid_reduce<2>(acc, partials, counter, [&](double* t) {
         sc->rho_old = sc->rho;
         sc->rho = t[0];
@@ -752,6 +878,18 @@ __global__ void k_cn_finish(long long n, const T* __restrict__ u, const T* __res
         ustar[q] = u[q] + x[q];
 }
 
+// Persistent launch of the tiled flux kernels: as many blocks as fit on the GPU at once (measured
+// for the heaviest of them at set-up), each walking tiles until none is left.
+int g_tile_blocks[2] = {2 * IBM_NSM, 2 * IBM_NSM};   // FP32, FP64
+
+template <class T>
+dim3 tile_grid(const LesCtx& c) {
+    const long long items = (long long)((c.D.nx + FT_X - 1) / FT_X) * ((c.D.ny + FT_Y - 1) / FT_Y) *
+                            ((c.D.nz + FT_KZ - 1) / FT_KZ);
+    const long long cap = g_tile_blocks[sizeof(T) == 8];
+    return dim3((unsigned)(items < cap ? items : cap));
+}
+
 template <class T>
 int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T* ustar, int* iters, cudaStream_t s) {
     CNWork& w = *c.cn;
@@ -761,21 +899,20 @@ int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T*
     const unsigned nbv = lin_blocks(n3, 256);
     T *r = (T*)w.r, *rh = (T*)w.rh, *p = (T*)w.p, *v = (T*)w.v, *sv = (T*)w.sv, *tv = (T*)w.tv, *x = (T*)w.x;
     const T nu = (T)c.nu, gam = (T)c.quick, dt = (T)c.dt, hdt = (T)(0.5 * c.dt);
-    const int mrg = c.flux_margin;
     const unsigned ngen = lin_blocks(c.n_general > 0 ? c.n_general : 1, 256);
     prof_begin(c.prof, PS_PREDICT, s);
-    k_cn_begin<T, false><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol,
-                                                        w.maxit, w.sc, c.partials, c.counter, nullptr, 0, mrg);
+    k_cn_begin<T, false><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol,
+                                                        w.maxit, w.sc, c.partials, c.counter, nullptr, 0);
     k_cn_begin<T, true><<<ngen, 256, 0, s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol, w.maxit,
-                                             w.sc, c.partials, c.counter, c.general, c.n_general, mrg);
+                                             w.sc, c.partials, c.counter, c.general, c.n_general);
     prof_end(c.prof, PS_PREDICT, s);
     IBM_LAUNCHED("k_cn_begin");
     IBM_COUNT(c, 2);
     auto apply = [&](const T* in, T* out, int mode) {
-        k_cn_apply<T, false><<<c.pgrid, c.cg.block, 0, s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc,
-                                                            c.partials, c.counter, nullptr, 0, mrg);
+        k_cn_apply<T, false><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc,
+                                                            c.partials, c.counter, nullptr, 0);
         k_cn_apply<T, true><<<ngen, 256, 0, s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc, c.partials,
-                                                 c.counter, c.general, c.n_general, mrg);
+                                                 c.counter, c.general, c.n_general);
     };
     for (;;) {
         prof_begin(c.prof, PS_MOMENTUM, s);
@@ -808,7 +945,7 @@ int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T*
 
 namespace {
 // Order-preserving compaction of the general cells: one block per (y, z) row, ballots over x.
-__global__ void k_list_general(Dom D, int mrg, const unsigned long long* __restrict__ row_off,
+__global__ void k_list_general(Dom D, const unsigned long long* __restrict__ row_off,
                                int32_t* __restrict__ list) {
     const int j = blockIdx.x, k = blockIdx.y;
     __shared__ int base;
@@ -818,7 +955,7 @@ __global__ void k_list_general(Dom D, int mrg, const unsigned long long* __restr
     for (int i0 = 0; i0 < D.nx; i0 += 32) {
         const int i = i0 + threadIdx.x;
         const long long P = i + (long long)D.sy * j + D.sz * k;
-        const bool g = i < D.nx && !fast_cell(D, P, i, j, k, mrg);
+        const bool g = i < D.nx && !fast_cell(D, P, i, j, k);
         const unsigned m = __ballot_sync(0xffffffffu, g);
         if (g) list[row_off[row] + base + __popc(m & ((1u << threadIdx.x) - 1u))] = (int32_t)P;
         __syncwarp();
@@ -827,12 +964,14 @@ __global__ void k_list_general(Dom D, int mrg, const unsigned long long* __restr
     }
 }
 
-__global__ void k_row_counts(Dom D, int mrg, unsigned long long* __restrict__ rc) {
+__global__ void k_row_counts(Dom D, unsigned long long* __restrict__ rc, uint8_t* __restrict__ fast) {
     const int j = blockIdx.x, k = blockIdx.y;
     unsigned n = 0;
     for (int i = threadIdx.x; i < D.nx; i += 32) {
         const long long P = i + (long long)D.sy * j + D.sz * k;
-        n += !fast_cell(D, P, i, j, k, mrg);
+        const bool f = fast_cell(D, P, i, j, k);
+        fast[P] = f ? 1 : 0;
+        n += !f;
     }
     for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
     if (threadIdx.x == 0) rc[j + (long long)D.ny * k] = n;
@@ -850,25 +989,49 @@ __global__ void k_row_scan(long long nrows, unsigned long long* __restrict__ rc,
 }
 }  // namespace
 
+int flux_kernels_setup() {
+    // the FP64 tiles need more than the default 48 KB of dynamic shared memory
+    const int bytes = (int)fast_tile_smem<double>();
+    IBM_CUDA(cudaFuncSetAttribute(k_predict<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    IBM_CUDA(cudaFuncSetAttribute(k_cn_begin<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    IBM_CUDA(cudaFuncSetAttribute(k_cn_apply<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int dev = 0, nsm = IBM_NSM, bf = 0, bd = 0;
+    IBM_CUDA(cudaGetDevice(&dev));
+    IBM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    IBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_cn_apply<float, false>, FT_X * FT_Y,
+                                                           fast_tile_smem<float>()));
+    IBM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_cn_apply<double, false>, FT_X * FT_Y,
+                                                           fast_tile_smem<double>()));
+    g_tile_blocks[0] = (bf > 0 ? bf : 1) * nsm;
+    g_tile_blocks[1] = (bd > 0 ? bd : 1) * nsm;
+    return IBM_OK;
+}
+
 int build_general_list(LesCtx& c, cudaStream_t s) {
     const long long nrows = (long long)c.D.ny * c.D.nz;
     unsigned long long* rc = nullptr;
     IBM_CUDA(cudaMalloc((void**)&rc, (size_t)(nrows + 1) * sizeof(unsigned long long)));
     dim3 rows((unsigned)c.D.ny, (unsigned)c.D.nz);
-    k_row_counts<<<rows, 32, 0, s>>>(c.D, c.flux_margin, rc);
+    cudaError_t e0 = cudaMalloc((void**)&c.fastmask, (size_t)c.D.N);
+    if (e0 != cudaSuccess) {
+        cudaFree(rc);
+        return ibm_fail(IBM_E_NOMEM, "momentum flux: fast-cell mask (%lld bytes)", (long long)c.D.N);
+    }
+    k_row_counts<<<rows, 32, 0, s>>>(c.D, rc, c.fastmask);
     k_row_scan<<<1, 1, 0, s>>>(nrows, rc, rc + nrows);
     unsigned long long total = 0;
     cudaError_t e = cudaMemcpyAsync(&total, rc + nrows, sizeof(total), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c.general, (size_t)(total > 0 ? total : 1) * sizeof(int32_t));
     if (e == cudaSuccess && total > 0) {
-        k_list_general<<<rows, 32, 0, s>>>(c.D, c.flux_margin, rc, c.general);
+        k_list_general<<<rows, 32, 0, s>>>(c.D, rc, c.general);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(rc);
     if (e != cudaSuccess) return ibm_cuda_check(e, "momentum flux: general-cell list");
     c.n_general = (long long)total;
+    c.D.fast = c.fastmask;
     return IBM_OK;
 }
 
@@ -885,13 +1048,12 @@ int launch_csm(const LesCtx& c, const void* u, void* nut, cudaStream_t s) {
 template <class T>
 static void predict_t(const LesCtx& c, const T* u, const T* U, const T* nut, const T* Hprev, T* H, T* ustar, int first,
                       cudaStream_t s) {
-    const int mrg = c.flux_margin;
-    k_predict<false, T><<<c.pgrid, c.cg.block, 0, s>>>(c.D, c.F, u, U, nut, Hprev, H, ustar, (T)c.nu, (T)c.dt, first,
-                                                       (T)c.quick, nullptr, 0, mrg);
+    k_predict<false, T><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(c.D, c.F, u, U, nut, Hprev, H, ustar, (T)c.nu, (T)c.dt, first,
+                                                       (T)c.quick, nullptr, 0);
     if (c.n_general > 0)
         k_predict<true, T><<<lin_blocks(c.n_general, 256), 256, 0, s>>>(c.D, c.F, u, U, nut, Hprev, H, ustar,
                                                                          (T)c.nu, (T)c.dt, first, (T)c.quick,
-                                                                         c.general, c.n_general, mrg);
+                                                                         c.general, c.n_general);
 }
 
 int launch_predict(const LesCtx& c, const void* u, const void* U, const void* nut, const void* Hprev, void* H,
@@ -969,10 +1131,10 @@ int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s) {
 
 template <class T>
 static void correct_t(const LesCtx& c, const T* us, const T* Us, const double* p, T* u, T* U, cudaStream_t s) {
-    k_correct_cells<T><<<c.pgrid, c.cg.block, 0, s>>>(c.D, us, p, u, c.dt);
+    k_correct_cells<T><<<c.pgrid, c.cg.block, 0, s>>>(c.D, us, p, u, (T)(c.dt / (2.0 * c.D.dx)));
     for (int a = 0; a < 3; ++a) {
         const long long nf = (long long)c.F.dim[a][0] * c.F.dim[a][1] * c.F.dim[a][2];
-        k_correct_faces<T><<<lin_blocks(nf, 256), 256, 0, s>>>(c.D, c.F, a, Us, p, U, c.dt);
+        k_correct_faces<T><<<lin_blocks(nf, 256), 256, 0, s>>>(c.D, c.F, a, Us, p, U, (T)(c.dt / c.D.dx));
     }
 }
 

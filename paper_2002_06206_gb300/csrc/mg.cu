@@ -12,11 +12,23 @@
 // coarsest grid) is a symmetric operator, as CG requires.
 //
 // Equations are solved in the unscaled form  sum_links g (x_N - x_P) - d x_P = dx^2 r.
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "solver.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace {
+
+#define MG_TAIL_CTAS 8          // portable cluster size
+#define MG_TAIL_MAX_CELLS (1LL << 13)
+
+struct MGTail {
+    MGLev lev[IBM_MG_MAXLEV];
+    int first, nlev, sweeps, coarse_sweeps;
+    double omega;
+};
 
 __device__ __forceinline__ unsigned flags_at(const Dom& D, long long P) { return D.flags ? (unsigned)D.flags[P] : 0u; }
 
@@ -60,10 +72,14 @@ __device__ __forceinline__ void coarse_links(const MGLev& L, long long P, const 
     }
 }
 
+// Cell coordinates from a linear index (grids hold fewer than 2^31 cells: 32-bit division).
 __device__ __forceinline__ void coords3(long long c, int nx, int ny, int x[3]) {
-    x[0] = (int)(c % nx);
-    x[1] = (int)((c / nx) % ny);
-    x[2] = (int)(c / ((long long)nx * ny));
+    const unsigned u = (unsigned)c, unx = (unsigned)nx, uny = (unsigned)ny;
+    const unsigned r = u / unx;
+    x[0] = (int)(u - r * unx);
+    const unsigned z = r / uny;
+    x[1] = (int)(r - z * uny);
+    x[2] = (int)z;
 }
 
 // ---- set-up -------------------------------------------------------------------------------------
@@ -185,18 +201,25 @@ __global__ void __launch_bounds__(256) k_mg_smooth0(Dom D, const T* __restrict__
     }
 }
 
+// One red-black pass of colour `col` on a coarse level.  Work item t covers the t-th cell of that
+// colour (row-major over the half-rows), t = t0, t0 + nt, ...; with `zero` the iterate is taken as 0
+// and the cell of the other colour next to it is cleared.
 template <class T>
-__global__ void __launch_bounds__(256) k_mg_smoothc(MGLev L, int col, int zero, const SolveScal* sc) {
-    if (sc->done) return;
+__device__ __forceinline__ void smooth_level(const MGLev& L, int col, bool zero, long long t0, long long nt) {
     const T* __restrict__ b = (const T*)L.b;
     T* __restrict__ x = (T*)L.x;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L.N; q += (long long)gridDim.x * blockDim.x) {
+    const int hx = (L.nx + 1) >> 1;
+    const long long n = (long long)hx * L.ny * L.nz;
+    for (long long t = t0; t < n; t += nt) {
         int c[3];
-        coords3(q, L.nx, L.ny, c);
-        if (((c[0] + c[1] + c[2]) & 1) != col) {
-            if (zero) x[q] = (T)0;
-            continue;
-        }
+        coords3(t, hx, L.ny, c);
+        const int par = (col + c[1] + c[2]) & 1;
+        const int x0 = 2 * c[0] + par, x1 = 2 * c[0] + (par ^ 1);
+        const long long row = L.sy * c[1] + L.sz * c[2];
+        if (zero && x1 < L.nx) x[row + x1] = (T)0;
+        if (x0 >= L.nx) continue;
+        c[0] = x0;
+        const long long q = row + x0;
         const float inv = L.invdg[q];
         if (inv == 0.f) { x[q] = (T)0; continue; }
         T s = 0;
@@ -210,6 +233,13 @@ __global__ void __launch_bounds__(256) k_mg_smoothc(MGLev L, int col, int zero, 
         }
         x[q] = (s - b[q]) * (T)inv;
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_smoothc(MGLev L, int col, int zero, const SolveScal* sc) {
+    if (sc->done) return;
+    smooth_level<T>(L, col, zero != 0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                    (long long)gridDim.x * blockDim.x);
 }
 
 // Residual of level 0 restricted to level 1: each coarse cell sums the residuals of its children.
@@ -240,14 +270,14 @@ __global__ void k_mg_restrict0(Dom D, const T* __restrict__ r, const T* __restri
     }
 }
 
+// Residual of coarse level F restricted to level C (sum over the children).
 template <class T>
-__global__ void k_mg_restrictc(MGLev F, MGLev C, const SolveScal* sc) {
-    if (sc->done) return;
+__device__ __forceinline__ void restrict_level(const MGLev& F, const MGLev& C, long long t0, long long nt) {
     const T* __restrict__ bf = (const T*)F.b;
     const T* __restrict__ xf = (const T*)F.x;
     T* __restrict__ bc = (T*)C.b;
     const int n[3] = {F.nx, F.ny, F.nz};
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.N; q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = t0; q < C.N; q += nt) {
         int X[3];
         coords3(q, C.nx, C.ny, X);
         T acc = 0;
@@ -271,13 +301,18 @@ __global__ void k_mg_restrictc(MGLev F, MGLev C, const SolveScal* sc) {
     }
 }
 
+template <class T>
+__global__ void k_mg_restrictc(MGLev F, MGLev C, const SolveScal* sc) {
+    if (sc->done) return;
+    restrict_level<T>(F, C, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 // Coarse correction: x_fine += omega * x_coarse(parent), level 0 or a coarse level.
 template <class T>
-__global__ void k_mg_prolong(long long N, int nx, int ny, T* __restrict__ xf, const MGLev C, T omega,
-                             const SolveScal* sc) {
-    if (sc->done) return;
+__device__ __forceinline__ void prolong_level(long long N, int nx, int ny, T* __restrict__ xf, const MGLev& C, T omega,
+                                              long long t0, long long nt) {
     const T* __restrict__ xc = (const T*)C.x;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = t0; q < N; q += nt) {
         int x[3];
         coords3(q, nx, ny, x);
         const long long parent = (x[0] >> 1) + C.sy * (x[1] >> 1) + C.sz * (x[2] >> 1);
@@ -285,13 +320,19 @@ __global__ void k_mg_prolong(long long N, int nx, int ny, T* __restrict__ xf, co
     }
 }
 
+template <class T>
+__global__ void k_mg_prolong(long long N, int nx, int ny, T* __restrict__ xf, const MGLev C, T omega,
+                             const SolveScal* sc) {
+    if (sc->done) return;
+    prolong_level<T>(N, nx, ny, xf, C, omega, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                     (long long)gridDim.x * blockDim.x);
+}
+
 // Coarsest level (at most 1024 cells, one block of 1024 threads, one cell per thread): `sweeps`
 // red-black passes then as many black-red (a symmetric operator).  Each thread keeps its links and
 // right-hand side in registers; the iterate lives in shared memory.
 template <class T>
-__global__ void __launch_bounds__(1024) k_mg_coarsest(MGLev L, int sweeps, const SolveScal* sc) {
-    if (sc->done) return;
-    __shared__ T xs[1024];
+__device__ __forceinline__ void coarsest_solve(const MGLev& L, int sweeps, T* xs) {
     const long long q = threadIdx.x;
     const bool act = q < L.N;
     int col = 0;
@@ -326,6 +367,55 @@ __global__ void __launch_bounds__(1024) k_mg_coarsest(MGLev L, int sweeps, const
     if (act) ((T*)L.x)[q] = xs[threadIdx.x];
 }
 
+template <class T>
+__global__ void __launch_bounds__(1024) k_mg_coarsest(MGLev L, int sweeps, const SolveScal* sc) {
+    if (sc->done) return;
+    __shared__ T xs[1024];
+    coarsest_solve<T>(L, sweeps, xs);
+}
+
+// The small levels first .. nlev-1 of a V-cycle in one launch: one cluster of MG_TAIL_CTAS blocks of
+// 1024 threads walks the descent (smoothing, restriction), the coarsest solve (block 0) and the
+// ascent (prolongation, smoothing), with a cluster barrier (hardware, release/acquire at cluster
+// scope) between dependent passes.  These levels are a few MB at most and stay in L2; as separate
+// kernels each pass would cost a launch for a few microseconds of work.
+template <class T>
+__global__ void __launch_bounds__(1024) k_mg_tail(MGTail M, const SolveScal* sc) {
+    if (sc->done) return;                       // the flag is uniform: set by an earlier kernel
+    __shared__ T xs[1024];
+    cg::cluster_group cl = cg::this_cluster();
+    const long long t0 = (long long)cl.block_rank() * blockDim.x + threadIdx.x;
+    const long long nt = (long long)cl.num_blocks() * blockDim.x;
+    auto bar = [&]() {
+        __threadfence();
+        cl.sync();
+    };
+    const int last = M.nlev - 1;
+    for (int l = M.first; l < last; ++l) {
+        for (int q = 0; q < M.sweeps; ++q) {
+            smooth_level<T>(M.lev[l], 0, q == 0, t0, nt);
+            bar();
+            smooth_level<T>(M.lev[l], 1, false, t0, nt);
+            bar();
+        }
+        restrict_level<T>(M.lev[l], M.lev[l + 1], t0, nt);
+        bar();
+    }
+    if (cl.block_rank() == 0) coarsest_solve<T>(M.lev[last], M.coarse_sweeps, xs);
+    bar();
+    for (int l = last - 1; l >= M.first; --l) {
+        const MGLev& F = M.lev[l];
+        prolong_level<T>(F.N, F.nx, F.ny, (T*)F.x, M.lev[l + 1], (T)M.omega, t0, nt);
+        bar();
+        for (int q = 0; q < M.sweeps; ++q) {
+            smooth_level<T>(F, 1, false, t0, nt);
+            bar();
+            smooth_level<T>(F, 0, false, t0, nt);
+            bar();
+        }
+    }
+}
+
 // Last pass of the V-cycle on level 0 (colour 0) fused with rho = (r, z) over both colours.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_final0(Dom D, const T* __restrict__ r, T* __restrict__ z, T scale,
@@ -352,7 +442,7 @@ __global__ void __launch_bounds__(256) k_mg_final0(Dom D, const T* __restrict__ 
             }
         }
     }
-    double acc[1] = {(double)part};
+    decltype(part) acc[1] = {part};
     grid_reduce<1>(acc, partials, counter, [&](double* t) {
         sc->rz_old = sc->rz;
         sc->rz = t[0];
@@ -420,29 +510,63 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
     }
     if (mg.nlev > 1) {
         prof_begin(c.prof, PS_MG_TRANSFER, s);
-        k_mg_restrict0<T><<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, r, z, scale, mg.lev[1], sc);
+        if constexpr (std::is_same<T, float>::value) {
+            if (vec) launch_mg_restrict0_x4(c, r, z, scale, mg.lev[1], sc, s);
+            else k_mg_restrict0<T><<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, r, z, scale, mg.lev[1], sc);
+        } else {
+            k_mg_restrict0<T><<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, r, z, scale, mg.lev[1], sc);
+        }
         prof_end(c.prof, PS_MG_TRANSFER, s);
         ++launches;
         prof_begin(c.prof, PS_MG_COARSE, s);
-        for (int l = 1; l + 1 < mg.nlev; ++l) {
+        // levels >= tf (if any) run in one cluster launch; separate kernels above them
+        int tf = mg.nlev;
+        for (int l = 1; l + 1 < mg.nlev; ++l)
+            if (mg.lev[l].N <= MG_TAIL_MAX_CELLS) { tf = l; break; }
+        const int top = tf < mg.nlev ? tf : mg.nlev - 1;
+        for (int l = 1; l < top; ++l) {
             const MGLev& L = mg.lev[l];
             for (int q = 0; q < S; ++q) {
-                k_mg_smoothc<T><<<lin_blocks(L.N), 256, 0, s>>>(L, 0, q == 0, sc);
-                k_mg_smoothc<T><<<lin_blocks(L.N), 256, 0, s>>>(L, 1, 0, sc);
+                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, q == 0, sc);
+                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
                 launches += 2;
             }
             k_mg_restrictc<T><<<lin_blocks(mg.lev[l + 1].N), 256, 0, s>>>(L, mg.lev[l + 1], sc);
             ++launches;
         }
-        k_mg_coarsest<T><<<1, 1024, 0, s>>>(mg.lev[mg.nlev - 1], mg.coarse_sweeps, sc);
-        ++launches;
-        for (int l = mg.nlev - 2; l >= 1; --l) {
+        if (tf < mg.nlev) {
+            MGTail M;
+            for (int l = 0; l < mg.nlev; ++l) M.lev[l] = mg.lev[l];
+            M.first = tf;
+            M.nlev = mg.nlev;
+            M.sweeps = S;
+            M.coarse_sweeps = mg.coarse_sweeps;
+            M.omega = mg.omega;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(MG_TAIL_CTAS);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = MG_TAIL_CTAS;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            IBM_CUDA(cudaLaunchKernelEx(&cfg, k_mg_tail<T>, M, (const SolveScal*)sc));
+            ++launches;
+        } else {
+            k_mg_coarsest<T><<<1, 1024, 0, s>>>(mg.lev[mg.nlev - 1], mg.coarse_sweeps, sc);
+            ++launches;
+        }
+        for (int l = top - 1; l >= 1; --l) {
             const MGLev& L = mg.lev[l];
             k_mg_prolong<T><<<lin_blocks(L.N), 256, 0, s>>>(L.N, L.nx, L.ny, (T*)L.x, mg.lev[l + 1], om, sc);
             ++launches;
             for (int q = 0; q < S; ++q) {
-                k_mg_smoothc<T><<<lin_blocks(L.N), 256, 0, s>>>(L, 1, 0, sc);
-                k_mg_smoothc<T><<<lin_blocks(L.N), 256, 0, s>>>(L, 0, 0, sc);
+                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
+                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, 0, sc);
                 launches += 2;
             }
         }

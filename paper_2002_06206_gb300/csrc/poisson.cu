@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_residual(Dom D, const double* __restric
             part1 += rt * rt;
         }
     }
-    double acc[2] = {(double)part0, (double)part1};
+    decltype(part0) acc[2] = {part0, part1};
     grid_reduce<2>(acc, partials, counter, [&](double* t) {
         sc->res2 = t[0];
         sc->rr = t[1];
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_cg_dir_spmv(Dom D, const T* __restrict_
             part += pc * qv;
         }
     }
-    double acc[1] = {(double)part};
+    decltype(part) acc[1] = {part};
     grid_reduce<1>(acc, partials, counter, [&](double* t) { sc->pq = t[0]; });
 }
 
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_cg_update(long long N, const T* __restr
         r[c] = rv;
         part += rv * rv;
     }
-    double acc[1] = {(double)part};
+    decltype(part) acc[1] = {part};
     grid_reduce<1>(acc, partials, counter, [&](double* t) {
         sc->rr_old = sc->rr;
         sc->rr = t[0];
@@ -310,13 +310,13 @@ __global__ void __launch_bounds__(256) k_bicg_pv(Dom D, const T* __restrict__ r,
     const T beta = restart ? (T)0 : (T)((sc->rho / sc->rho_old) * (sc->alpha / sc->omega));
     const T om = restart ? (T)0 : (T)sc->omega;
     auto pv = [&](long long c) { return restart ? r[c] : r[c] + beta * (pold[c] - om * vold[c]); };
-    double acc[1] = {0.0};
+    T acc[1] = {(T)0};
     CELL_LOOP_BEGIN
     const T pc = pv(P);
     const T v = apply_at<T>(D, P, x, fl, pc, pv) * idx2;
     pnew[P] = pc;
     vnew[P] = v;
-    acc[0] += (double)rh[P] * (double)v;
+    acc[0] += rh[P] * v;
     CELL_LOOP_END
     grid_reduce<1>(acc, partials, counter, [&](double* t) {
         sc->rv = t[0];
@@ -332,15 +332,15 @@ __global__ void __launch_bounds__(256) k_bicg_st(Dom D, const T* __restrict__ r,
     if (sc->done) return;
     const T alpha = (T)sc->alpha;
     auto sf = [&](long long c) { return r[c] - alpha * v[c]; };
-    double acc[3] = {0.0, 0.0, 0.0};
+    T acc[3] = {(T)0, (T)0, (T)0};
     CELL_LOOP_BEGIN
     const T sc_ = sf(P);
     const T t = apply_at<T>(D, P, x, fl, sc_, sf) * idx2;
     sv[P] = sc_;
     tv[P] = t;
-    acc[0] += (double)t * (double)sc_;
-    acc[1] += (double)t * (double)t;
-    acc[2] += (double)sc_ * (double)sc_;
+    acc[0] += t * sc_;
+    acc[1] += t * t;
+    acc[2] += sc_ * sc_;
     CELL_LOOP_END
     grid_reduce<3>(acc, partials, counter, [&](double* t) {
         sc->ts = t[0];
@@ -356,13 +356,13 @@ __global__ void __launch_bounds__(256) k_bicg_xr(long long N, const T* __restric
                                                  T* __restrict__ r, SolveScal* sc, double* partials, unsigned* counter) {
     if (sc->done) return;
     const T alpha = (T)sc->alpha, om = (T)sc->omega;
-    double acc[2] = {0.0, 0.0};
+    T acc[2] = {(T)0, (T)0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         x[c] = x[c] + alpha * p[c] + om * sv[c];
         const T rv = sv[c] - om * tv[c];
         r[c] = rv;
-        acc[0] += (double)rh[c] * (double)rv;
-        acc[1] += (double)rv * (double)rv;
+        acc[0] += rh[c] * rv;
+        acc[1] += rv * rv;
     }
     grid_reduce<2>(acc, partials, counter, [&](double* t) {
         sc->rho_old = sc->rho;
@@ -514,22 +514,25 @@ __global__ void __launch_bounds__(256) k_two_residuals(Dom D, const double* __re
     const int i = blockIdx.x * IBM_TX + threadIdx.x, j = blockIdx.y * IBM_TY + threadIdx.y;
     const int kb = blockIdx.z * IBM_KU;
     const bool active = i < D.nx && j < D.ny;
+    // only compares the two starting points, so FP32 arithmetic on the rounded iterates suffices
     float p0 = 0.f, p1 = 0.f;
-    auto va = [&](long long n) { return xa[n]; };
-    auto vb = [&](long long n) { return xb[n]; };
+    const float fidx2 = (float)idx2;
+    auto va = [&](long long n) { return (float)xa[n]; };
+    auto vb = [&](long long n) { return (float)xb[n]; };
 #pragma unroll
     for (int u = 0; u < IBM_KU; ++u) {
         const int k = kb + u;
         if (active && k < D.nz) {
             const long long P = i + (long long)D.sy * j + D.sz * k;
             const unsigned fl = D.flags ? (unsigned)D.flags[P] : 0u;
-            const float ra = (float)(b[P] - link_sum7<double>(D, P, i, j, k, fl, xa[P], va) * idx2);
-            const float rb = (float)(b[P] - link_sum7<double>(D, P, i, j, k, fl, xb[P], vb) * idx2);
+            const float bp = (float)b[P];
+            const float ra = bp - link_sum7<float>(D, P, i, j, k, fl, (float)xa[P], va) * fidx2;
+            const float rb = bp - link_sum7<float>(D, P, i, j, k, fl, (float)xb[P], vb) * fidx2;
             p0 += ra * ra;
             p1 += rb * rb;
         }
     }
-    double acc[2] = {(double)p0, (double)p1};
+    decltype(p0) acc[2] = {p0, p1};
     grid_reduce<2>(acc, partials, counter, [&](double* t) {
         out[0] = t[0];
         out[1] = t[1];

@@ -84,12 +84,14 @@ struct LesCtx {
     MG* mg;                   // multigrid preconditioner, null for plain CG
     int integrator;           // IBM_ADAMS_BASHFORTH or IBM_CRANK_NICOLSON
     CNWork* cn;               // Crank-Nicolson workspace, null for Adams-Bashforth
-    int flux_margin;          // momentum flux: 2 with QUICK, else 1
     int32_t* general;         // cells the momentum flux evaluates with the general rules
     long long n_general;
+    uint8_t* fastmask;        // N bytes: 1 for the cells of the tiled fast path
 };
 // les.cu: list of the cells that are not fast_cell for the momentum flux (c.general, c.n_general).
 int build_general_list(LesCtx& c, cudaStream_t s);
+// les.cu: kernel attributes of the tiled momentum-flux kernels (once per process and device).
+int flux_kernels_setup();
 
 #define IBM_COUNT(c, n) \
     do { if ((c).nlaunch) *(c).nlaunch += (n); } while (0)
@@ -111,6 +113,8 @@ int launch_forces(const LesCtx& c, const float* tri, long long ntri, const doubl
 
 // poisson.cu
 // stencil4.cu: FP32 fine-grid kernels with 4 cells per thread (nx a multiple of 4)
+void launch_mg_restrict0_x4(const LesCtx& c, const float* r, const float* z, float scale, const MGLev& C,
+                            SolveScal* sc, cudaStream_t s);
 bool x4_ok(const LesCtx& c);
 void launch_cg_dir_spmv_x4(const LesCtx& c, const float* src, const float* pold, float* pnew, float* q, float idx2,
                            SolveScal* sc, int pcg, cudaStream_t s);

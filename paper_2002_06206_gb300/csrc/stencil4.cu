@@ -37,7 +37,7 @@ __device__ __forceinline__ unsigned flags4(const Dom& D, long long P) {
 }
 
 // CG first half (see poisson.cu): p = src + beta p_old, q = A p, (p, q).
-__global__ void __launch_bounds__(256) k_cg_dir_spmv_x4(Dom D, const float* __restrict__ r,
+__global__ void __launch_bounds__(256, 4) k_cg_dir_spmv_x4(Dom D, const float* __restrict__ r,
                                                         const float* __restrict__ pold, float* __restrict__ pnew,
                                                         float* __restrict__ q, float idx2, SolveScal* sc,
                                                         double* partials, unsigned* counter, int pcg) {
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_cg_dir_spmv_x4(Dom D, const float* __re
         part += (pc[0] * qv[0] + pc[1] * qv[1]) + (pc[2] * qv[2] + pc[3] * qv[3]);
     }
     X4_TILE_LOOP_END
-    double acc[1] = {(double)part};
+    decltype(part) acc[1] = {part};
     grid_reduce<1>(acc, partials, counter, [&](double* t) { sc->pq = t[0]; });
 }
 
@@ -105,10 +105,36 @@ __device__ __forceinline__ float gs_generic(const Dom& D, const float* r, const 
     return dg == 0.f ? 0.f : (s - scale * r[P]) / dg;
 }
 
+// Gauss-Seidel update of cells C0 and C0 + 2 of a plain chunk (compile-time positions, so every
+// element access is a register).
+template <int C0>
+__device__ __forceinline__ void gs_plain(float (&zc)[4], const float4& r4, const float* z, long long P, const Dom& D,
+                                         float scale, bool zero) {
+    const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+    if (zero) {
+        zc[C0] = -scale * rr[C0] * (1.f / 6.f);
+        zc[C0 + 2] = -scale * rr[C0 + 2] * (1.f / 6.f);
+        return;
+    }
+    const float4 ym4 = ld4(z + P - D.sy), yp4 = ld4(z + P + D.sy);
+    const float4 zm4 = ld4(z + P - D.sz), zp4 = ld4(z + P + D.sz);
+    const float ym[4] = {ym4.x, ym4.y, ym4.z, ym4.w}, yp[4] = {yp4.x, yp4.y, yp4.z, yp4.w};
+    const float zm[4] = {zm4.x, zm4.y, zm4.z, zm4.w}, zp[4] = {zp4.x, zp4.y, zp4.z, zp4.w};
+    const float xl = C0 == 0 ? z[P - 1] : 0.f, xr = C0 == 1 ? z[P + 4] : 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int m = C0 + 2 * h;
+        const float xm = m == 0 ? xl : zc[m - 1];
+        const float xp = m == 3 ? xr : zc[m + 1];
+        const float s = ((xm + xp) + (ym[m] + yp[m])) + (zm[m] + zp[m]);
+        zc[m] = (s - scale * rr[m]) * (1.f / 6.f);
+    }
+}
+
 // One red-black pass of colour `col` (see mg.cu), 4 cells per thread: the cells of the other colour
 // are read and written back unchanged, which no other thread modifies during the pass.  With `fin`
 // this is the last pass of the V-cycle (colour 0) and (r, z) over all cells is reduced as well.
-__global__ void __launch_bounds__(256) k_mg_smooth0_x4(Dom D, const float* __restrict__ r, float* z, float scale,
+__global__ void __launch_bounds__(256, 4) k_mg_smooth0_x4(Dom D, const float* __restrict__ r, float* z, float scale,
                                                        int col, int zero, int fin, SolveScal* sc, double* partials,
                                                        unsigned* counter) {
     if (sc->done) return;
@@ -130,35 +156,26 @@ __global__ void __launch_bounds__(256) k_mg_smooth0_x4(Dom D, const float* __res
             zc[0] = z4.x; zc[1] = z4.y; zc[2] = z4.z; zc[3] = z4.w;
         }
         if (plain_chunk(D, i0, j, k, fl4)) {
-            if (zero) {
-                zc[c0] = -scale * el(r4, c0) * (1.f / 6.f);
-                zc[c0 + 2] = -scale * el(r4, c0 + 2) * (1.f / 6.f);
-            } else {
-                const float4 ym = ld4(z + P - D.sy), yp = ld4(z + P + D.sy);
-                const float4 zm = ld4(z + P - D.sz), zp = ld4(z + P + D.sz);
-                const float xl = z[P - 1], xr = z[P + 4];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int m = c0 + 2 * h;
-                    const float xm = m == 0 ? xl : zc[m - 1];
-                    const float xp = m == 3 ? xr : zc[m + 1];
-                    const float s = ((xm + xp) + (el(ym, m) + el(yp, m))) + (el(zm, m) + el(zp, m));
-                    zc[m] = (s - scale * el(r4, m)) * (1.f / 6.f);
-                }
-            }
+            // the colour's two cells are m = c0 and c0 + 2; c0 is uniform across a warp (same j, k)
+            if (c0 == 0) gs_plain<0>(zc, r4, z, P, D, scale, zero != 0);
+            else gs_plain<1>(zc, r4, z, P, D, scale, zero != 0);
         } else {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int m = c0 + 2 * h;
                 const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
-                zc[m] = gs_generic(D, r, z, scale, P + m, i0 + m, j, k, fl, zero != 0);
+                const float g = gs_generic(D, r, z, scale, P + m, i0 + m, j, k, fl, zero != 0);
+                if (m == 0) zc[0] = g;
+                else if (m == 1) zc[1] = g;
+                else if (m == 2) zc[2] = g;
+                else zc[3] = g;
             }
         }
         st4(z + P, make_float4(zc[0], zc[1], zc[2], zc[3]));
         if (fin) part += (r4.x * zc[0] + r4.y * zc[1]) + (r4.z * zc[2] + r4.w * zc[3]);
     }
     X4_TILE_LOOP_END
-    double acc[1] = {(double)part};
+    decltype(part) acc[1] = {part};
     if (fin)
         grid_reduce<1>(acc, partials, counter, [&](double* t) {
             sc->rz_old = sc->rz;
@@ -166,9 +183,74 @@ __global__ void __launch_bounds__(256) k_mg_smooth0_x4(Dom D, const float* __res
         });
 }
 
+// Level-0 residual restricted to level 1, one thread per pair of coarse cells (X0, X0 + 1) at (Y, Z):
+// the 4 fine cells [4 X0', 4 X0' + 4) of each of the (up to) 4 fine rows below them, with 16-byte
+// loads.  b_C = sum over the children of  scale r - (sum_links g (z_N - z_P) - d z_P).
+__global__ void __launch_bounds__(256) k_mg_restrict0_x4(Dom D, const float* __restrict__ r,
+                                                         const float* __restrict__ z, float scale, MGLev C,
+                                                         const SolveScal* sc) {
+    if (sc->done) return;
+    float* __restrict__ bc = (float*)C.b;
+    const int px = D.nx / 4;                                  // coarse-cell pairs along x
+    const long long npairs = (long long)px * C.ny * C.nz;
+    auto zv = [&](long long c) { return z[c]; };
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int xp = (int)(t % px), Y = (int)((t / px) % C.ny), Z = (int)(t / ((long long)px * C.ny));
+        const int i0 = 4 * xp;
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj) {
+                const int j = 2 * Y + dj, k = 2 * Z + dk;
+                if (j >= D.ny || k >= D.nz) continue;
+                const long long P = i0 + (long long)D.sy * j + D.sz * k;
+                const unsigned fl4 = flags4(D, P);
+                const float4 r4 = ld4(r + P), z4 = ld4(z + P);
+                float res[4];
+                if (plain_chunk(D, i0, j, k, fl4)) {
+                    const float4 ym = ld4(z + P - D.sy), yp = ld4(z + P + D.sy);
+                    const float4 zm = ld4(z + P - D.sz), zp = ld4(z + P + D.sz);
+                    const float xl = z[P - 1], xr = z[P + 4];
+                    const float zc[4] = {z4.x, z4.y, z4.z, z4.w}, rr[4] = {r4.x, r4.y, r4.z, r4.w};
+                    const float a[4] = {ym.x + yp.x + zm.x + zp.x, ym.y + yp.y + zm.y + zp.y,
+                                        ym.z + yp.z + zm.z + zp.z, ym.w + yp.w + zm.w + zp.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float xm = m == 0 ? xl : zc[m - 1];
+                        const float xq = m == 3 ? xr : zc[m + 1];
+                        const float az = (xm + xq) + a[m] - 6.f * zc[m];
+                        res[m] = scale * rr[m] - az;
+                    }
+                } else {
+                    const float zc[4] = {z4.x, z4.y, z4.z, z4.w}, rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
+                        res[m] = scale * rr[m] - link_sum7<float>(D, P + m, i0 + m, j, k, fl, zc[m], zv);
+                    }
+                }
+                acc0 += res[0] + res[1];
+                acc1 += res[2] + res[3];
+            }
+        const long long q = 2 * xp + C.sy * Y + C.sz * Z;
+        bc[q] = acc0;
+        bc[q + 1] = acc1;
+    }
+}
+
 }  // namespace
 
 bool x4_ok(const LesCtx& c) { return (c.D.nx % 4) == 0; }
+
+void launch_mg_restrict0_x4(const LesCtx& c, const float* r, const float* z, float scale, const MGLev& C,
+                            SolveScal* sc, cudaStream_t s) {
+    const long long n = (long long)(c.D.nx / 4) * C.ny * C.nz;
+    long long b = (n + 255) / 256;
+    if (b > 8LL * IBM_NSM) b = 8LL * IBM_NSM;
+    k_mg_restrict0_x4<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(c.D, r, z, scale, C, sc);
+}
 
 dim3 x4_grid(const LesCtx& c) {
     const long long tiles = (long long)((c.D.nx / 4 + X4_TX - 1) / X4_TX) * ((c.D.ny + X4_TY - 1) / X4_TY) *
