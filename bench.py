@@ -52,6 +52,13 @@ def bytes_per_cell(s, integrator="cn"):
     }
 
 
+# the kernel behind each single-kernel group (FP32 path with nx a multiple of 4)
+GROUP_KERNEL = {"csm": "k_csm", "predict": "k_cn_begin (tiled + general)", "faces": "k_faces",
+                "rhs": "k_rhs", "residual": "k_residual", "cg_dir_spmv": "k_cg_dir_spmv_x4",
+                "cg_update": "k_cg_update", "correct": "k_correct_cells + k_correct_faces",
+                "mg_fine": "k_mg_smooth0_x4"}
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -73,7 +80,7 @@ def src_hash():
 
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -373,7 +380,7 @@ def run_ours(args):
     solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=cfg.precision, solver=L.CG, tol=cfg.tol,
                       max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
                       csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond,
-                      quick=args.quick, integrator=integ)
+                      quick=args.quick, integrator=integ, mg_sweeps=args.mg_sweeps)
     st = solver.fields(W.initial_fields(cfg))
     for _ in range(args.warmup):
         solver.step(st)
@@ -450,16 +457,26 @@ def run_ours(args):
     timed = {k: v for k, v in prof.items() if v[1] > 0 and k in bpc}
     everything = {k: v for k, v in prof.items() if v[1] > 0}
     M = float(np.mean(moms))
+    peak, peak_kind = read_peaks()
+    # every group with a byte model: achieved = algorithmic bytes per launch / mean launch time
+    groups = {}
+    for k, (ms_k, n_k) in timed.items():
+        gbs = bpc[k] * N / (ms_k / n_k * 1e-3) / 1e9
+        groups[k] = {"launches": n_k, "avg_launch_ms": ms_k / n_k, "bytes_per_launch": bpc[k] * N,
+                     "achieved_gbs": gbs, "frac": gbs / peak}
     if args.integrator == "cn" and prof["momentum"][1] > 0:
-        # the momentum BiCGStab as one launch per step: M iterations of p update (r, p, v -> p),
-        # two operator passes (input, U, nu_t, flags -> output, one dot operand) and s update
+        # the momentum BiCGStab per step (several kernel kinds): M iterations of p update (r, p, v ->
+        # p), two operator passes (input, U, nu_t, flags -> output, one dot operand), s update
         # (r, v -> s), x/r update (x, p, s, t, r_hat -> x, r): (68 s + 2) bytes per cell per iteration
-        bpc["momentum"] = M * (68 * s_bytes + 2)
-        timed["momentum"] = (prof["momentum"][0], args.steps)
+        mb = M * (68 * s_bytes + 2) * N
+        mms = prof["momentum"][0] / args.steps
+        groups["momentum_per_step"] = {"launches": args.steps, "avg_launch_ms": mms, "bytes_per_launch": mb,
+                                       "achieved_gbs": mb / (mms * 1e-3) / 1e9,
+                                       "frac": mb / (mms * 1e-3) / 1e9 / peak}
+    # the dominant single kernel (one kernel kind per launch of the group)
     dom = max(timed, key=lambda k: timed[k][0])
     avg_ms = timed[dom][0] / timed[dom][1]
     algo_bytes = bpc[dom] * N
-    peak, peak_kind = read_peaks()
     achieved = algo_bytes / (avg_ms * 1e-3) / 1e9
     shares = {k: round(v[0] / sum(x[0] for x in everything.values()), 4) for k, v in everything.items()}
 
@@ -478,16 +495,18 @@ def run_ours(args):
                        "triangles": int(len(tri)), "precision": "fp32 stencils and cg, fp64 residual refinement",
                        "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol,
                        "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
-                       "quick": args.quick, "momentum_bicgstab_iters_per_step": M,
+                       "quick": args.quick, "mg_sweeps": args.mg_sweeps if precond else None,
+                       "momentum_bicgstab_iters_per_step": M,
                        "timed_steps": [args.warmup + 1, args.warmup + args.steps],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (~0.4 GB of state per step vs 126 MB L2)",
                        "inner_iters_per_step": I, "refinements_per_step": float(np.mean(outers)),
                        "max_relres": float(np.max(relres))},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": dom, "kernel_name": GROUP_KERNEL.get(dom, dom),
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": ncu_traffic(dom),
                          "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ms,
-                         "peak_source": peak_kind, "shares": shares,
+                         "peak_source": peak_kind, "shares": shares, "groups": groups,
                          "note": "kernel times from a second pass of the same number of steps with per-kernel "
                                  "events (graphs off); shares are of event-timed kernel time"},
             "cpu_baseline": None if cpu is None else {
@@ -519,6 +538,7 @@ def main():
     ap.add_argument("--integrator", default="cn", choices=["cn", "ab2"],
                     help="Crank-Nicolson (the paper's production integrator) or Adams-Bashforth 2")
     ap.add_argument("--quick", type=float, default=0.1, help="QUICK fraction of the advected face value")
+    ap.add_argument("--mg-sweeps", type=int, default=2, help="red-black sweeps before and after each coarse correction")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -205,9 +205,16 @@ int poisson_apply(les_state* st, const double* d_p, double* d_Ap, void* stream);
 int poisson_solve(les_state* st, const double* d_b, double* d_p, double tol, int32_t max_it,
                   int32_t solver, les_stats* stats, void* stream);
 
-/* Eq. force: Shepard inverse-distance pressure on the front/back of every triangle,
- * F = sum_tri area (p_back - p_front) n.  out (host) = {Fx, Fy, Fz, triangles used}; synchronises. */
-int forces(les_state* st, const float* d_tri, int64_t ntri, const double* d_p, double out[4],
+/* Forces on the body (Sec. 3.2-3.3), out (host) = 12 doubles; synchronises.
+ *  out[0..2]  Eq. force: Shepard inverse-distance pressure on the front/back of every triangle,
+ *             F = sum_tri area (p_back - p_front) n;  out[3] = triangles used (both sides found);
+ *  out[4..6]  viscous force (reading; the paper integrates pressure): the molecular diffusive flux
+ *             nu (u_P - u_G) dx through every cut link, u_G the Eq. q_axis ghost value;
+ *             out[7] = links used (0 when d_u is NULL);
+ *  out[8..10] momentum-forcing estimate of the last les_step: -(sum of the forcing's du dx^3) / dt;
+ *  out[11]    0.
+ * d_u (may be NULL) is the cell velocity in the working precision. */
+int forces(les_state* st, const float* d_tri, int64_t ntri, const double* d_p, const void* d_u, double out[12],
            void* stream);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around each kernel group of

@@ -92,6 +92,7 @@ def lib():
                               C.c_int32, C.c_double, P]
         L.or_forces.argtypes = [P, P, i64, P, P]
         L.or_surface_pressure.argtypes = [P, P, i64, P, C.c_int, P, P]
+        L.or_viscous_force.argtypes = [P, P, P, P, i64, P, P, P]
         _lib = L
     return _lib
 
@@ -289,6 +290,14 @@ class Case:
         p = np.ascontiguousarray(p, np.float64)
         out = np.zeros(4)
         lib().or_forces(C.byref(self.g), _p(tri), len(tri), _p(p), _p(out))
+        return out
+
+    def viscous_force(self, u):
+        """Viscous force on the body from the cut links: [Fx, Fy, Fz, links]."""
+        u = np.ascontiguousarray(u, np.float64)
+        out = np.zeros(4)
+        lib().or_viscous_force(C.byref(self.g), C.byref(self.pr), _p(self.flags), _p(self.rec), len(self.rec),
+                               _p(self.cellrec), _p(u), _p(out))
         return out
 
     def surface_pressure(self, tri, p, zfilter=True):

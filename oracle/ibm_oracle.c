@@ -1127,3 +1127,25 @@ void or_surface_pressure(const or_grid* g, const float* tri, int64_t ntri, const
     out[2] = F[2];
     out[3] = (double)sides;
 }
+
+/* Viscous force on the body (reading; the paper integrates pressure only): the molecular diffusive
+ * momentum flux through every cut link, nu (u_P - u_G) / dx times the face area dx^2, with u_G the
+ * ghost value of Eq. q_axis -- exactly the flux the momentum equation exchanges with the wall there
+ * -- signed as a force on the body.  out[0..2] = force, out[3] = links used. */
+void or_viscous_force(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                      int64_t nrec, const int64_t* cellrec, const double* u, double out[4]) {
+    const int64_t N = ncells(g);
+    double F[3] = {0, 0, 0};
+    for (int64_t q = 0; q < nrec; ++q) {
+        const or_record* R = &rec[q];
+        const int64_t P = R->cell;
+        for (int c = 0; c < 3; ++c) {
+            double uG = or_velocity_across(g, pr, flags, rec, cellrec, u, c, P, (int)R->axis, (int)R->side);
+            F[c] += pr->nu * (u[c * N + P] - uG) * g->dx;
+        }
+    }
+    out[0] = F[0];
+    out[1] = F[1];
+    out[2] = F[2];
+    out[3] = (double)nrec;
+}

@@ -123,6 +123,11 @@ int or_step(const or_grid* g, const or_params* pr, const uint8_t* flags, const o
  * of triangles that contributed. */
 void or_forces(const or_grid* g, const float* tri, int64_t ntri, const double* p, double out[4]);
 
+/* Viscous force on the body: sum over cut links of nu (u_P - u_G) dx (u_G the Eq. q_axis ghost);
+ * out[0..2] = force, out[3] = links used. */
+void or_viscous_force(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+                      int64_t nrec, const int64_t* cellrec, const double* u, double out[4]);
+
 /* Surface pressure per triangle side (Eq. force) with, if zfilter, the thin-plate filter of
  * Eq. force_filter read as: a cell centre counts for node X only if the open segment from X to it
  * crosses no other triangle.  pside[2t] = front, pside[2t+1] = back Shepard average (NaN if that

@@ -213,6 +213,7 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     for (int a = 0; a < 3; ++a) c.D.u_in[a] = p->u_in[a];
     if (geom) {
         ibm_geom_device(geom, &c.D.flags, &c.D.cellrec, &c.D.rec, &c.inc, &c.n_rec, &c.n_inc);
+        c.D.nrec = c.n_rec;
     }
     c.F = make_faces(g->nx, g->ny, g->nz);
     c.NF = c.F.off[2] + (long long)c.F.dim[2][0] * c.F.dim[2][1] * c.F.dim[2][2];
@@ -234,7 +235,7 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     ALLOC(S->ustar, 3 * N * s);
     ALLOC(S->Ustar, (size_t)c.NF * s);
     ALLOC(S->b, N * 8);
-    ALLOC(S->out4, 4 * 8);
+    ALLOC(S->out4, 8 * 8);
     ALLOC(S->w.r, N * s);
     ALLOC(S->w.pa, N * s);
     ALLOC(S->w.pb, N * s);
@@ -257,7 +258,7 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
     ALLOC(c.fdelta, 3 * (size_t)(c.n_inc > 0 ? c.n_inc : 1) * sizeof(double));
     cudaError_t e;
     if ((e = cudaMallocHost((void**)&S->w.hsc, sizeof(SolveScal))) != cudaSuccess ||
-        (e = cudaMallocHost((void**)&S->hfs, 8 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&S->hfs, 16 * sizeof(double))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&S->w.ev, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMemset(c.counter, 0, 16 * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(S->nut, 0, N * s)) != cudaSuccess ||
@@ -266,7 +267,7 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
         free_state(S);
         return ibm_cuda_check(e, "les_create");
     }
-    memset(S->hfs, 0, 8 * sizeof(double));
+    memset(S->hfs, 0, 16 * sizeof(double));
     S->c.nlaunch = &S->nlaunch;
     {
         int rc1 = flux_kernels_setup();
@@ -520,6 +521,7 @@ extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int3
         prof_end(c.prof, PS_PREDICT, s);
     }
     const bool forcing = c.forcing_on && c.D.flags && c.n_inc > 0;
+    if (!forcing) S->hfs[0] = S->hfs[1] = S->hfs[2] = 0.0;
     if (forcing) {
         prof_begin(c.prof, PS_FORCING, s);
         if ((rc = launch_forcing(c, S->ustar, s))) return rc;
@@ -576,15 +578,24 @@ extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int3
     return IBM_OK;
 }
 
-extern "C" int forces(les_state* S, const float* tri, int64_t ntri, const double* p, double out[4], void* stream) {
+extern "C" int forces(les_state* S, const float* tri, int64_t ntri, const double* p, const void* u, double out[12],
+                      void* stream) {
     NEED(S); NEED(p); NEED(out);
     if (ntri < 0 || (ntri > 0 && !tri)) return ibm_fail(IBM_E_INVALID, "forces: bad soup");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = launch_forces(S->c, tri, ntri, p, S->out4, s);
     if (rc) return rc;
-    IBM_CUDA(cudaMemcpyAsync(S->hfs + 4, S->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (u) {
+        if ((rc = launch_viscous_force(S->c, u, S->out4 + 4, s))) return rc;
+    } else {
+        IBM_CUDA(cudaMemsetAsync(S->out4 + 4, 0, 4 * sizeof(double), s));
+    }
+    IBM_CUDA(cudaMemcpyAsync(S->hfs + 4, S->out4, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     IBM_CUDA(cudaStreamSynchronize(s));
-    memcpy(out, S->hfs + 4, 4 * sizeof(double));
+    memcpy(out, S->hfs + 4, 8 * sizeof(double));
+    // momentum-forcing estimate of the last step: the forcing added sum(du dx^3) to the fluid in dt
+    for (int q = 0; q < 3; ++q) out[8 + q] = -S->hfs[q] / S->c.dt;
+    out[11] = 0.0;
     return IBM_OK;
 }
 

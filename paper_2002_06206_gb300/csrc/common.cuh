@@ -37,6 +37,7 @@ struct Dom {
     const LinkRec* rec;
     int hom;                   // 1: ghost values without wall and inflow velocities (linear part)
     const uint8_t* fast;       // momentum flux: 1 where the tiled fast path applies (may be null)
+    long long nrec;            // link records (two per cut face)
 };
 
 __device__ __forceinline__ int link_bit(int a, int s) { return 2 * a + (s > 0); }

@@ -713,6 +713,31 @@ __global__ void k_forces(Dom D, const float* __restrict__ tri, long long ntri, c
     });
 }
 
+// Viscous force on the body: the molecular diffusive flux nu (u_P - u_G) dx through every cut link,
+// u_G the Eq. q_axis ghost value the momentum equation uses there.  One thread per link record.
+template <class T>
+__global__ void k_viscous_force(Dom D, const T* __restrict__ u, double nu, double* partials, unsigned* counter,
+                                double* out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long nrec = D.flags ? (long long)D.nrec : 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nrec; q += (long long)gridDim.x * blockDim.x) {
+        const LinkRec& R = D.rec[q];
+        const long long P = R.cell;
+        const int a = R.axis, sd = R.side;
+        const int xa = a == 0 ? (int)(P % D.nx) : (a == 1 ? (int)((P / D.nx) % D.ny) : (int)(P / D.sz));
+        const unsigned fl = D.flags[P];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double uG = (double)vel_across(D, u, c, P, xa, fl, a, sd);
+            acc[c] += nu * ((double)u[c * D.N + P] - uG) * D.dx;
+        }
+        acc[3] += 1.0;
+    }
+    grid_reduce<4>(acc, partials, counter, [&](double* t) {
+        for (int q = 0; q < 4; ++q) out[q] = t[q];
+    });
+}
+
 unsigned lin_blocks(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     long long cap = 16LL * IBM_NSM;
@@ -1152,6 +1177,17 @@ int launch_correct(const LesCtx& c, const void* ustar, const void* Ustar, const 
 int launch_forces(const LesCtx& c, const float* tri, long long ntri, const double* p, double* d_out4, cudaStream_t s) {
     k_forces<<<lin_blocks(ntri, 128), 128, 0, s>>>(c.D, tri, ntri, p, c.partials, c.counter, d_out4);
     IBM_LAUNCHED("k_forces");
+    IBM_COUNT(c, 1);
+    return IBM_OK;
+}
+
+int launch_viscous_force(const LesCtx& c, const void* u, double* d_out4, cudaStream_t s) {
+    const unsigned nb = lin_blocks(c.n_rec > 0 ? c.n_rec : 1, 256);
+    if (c.prec == IBM_FP64)
+        k_viscous_force<double><<<nb, 256, 0, s>>>(c.D, (const double*)u, c.nu, c.partials, c.counter, d_out4);
+    else
+        k_viscous_force<float><<<nb, 256, 0, s>>>(c.D, (const float*)u, c.nu, c.partials, c.counter, d_out4);
+    IBM_LAUNCHED("k_viscous_force");
     IBM_COUNT(c, 1);
     return IBM_OK;
 }

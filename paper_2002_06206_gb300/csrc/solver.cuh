@@ -108,6 +108,8 @@ int launch_faces(const LesCtx& c, const void* ustar, void* Ustar, cudaStream_t s
 int launch_rhs(const LesCtx& c, const void* Ustar, double* b, cudaStream_t s);
 int launch_correct(const LesCtx& c, const void* ustar, const void* Ustar, const double* p, void* u, void* U,
                    cudaStream_t s);
+// viscous force on the body from the cut links: d_out4 = {Fx, Fy, Fz, links}
+int launch_viscous_force(const LesCtx& c, const void* u, double* d_out4, cudaStream_t s);
 int launch_forces(const LesCtx& c, const float* tri, long long ntri, const double* p, double* d_out4,
                   cudaStream_t s);
 

@@ -92,7 +92,7 @@ SIGNATURES = {
     "poisson_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
                                 C.c_void_p, C.c_void_p]),
-    "forces": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "forces": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "les_num_faces": (C.c_int64, [C.c_void_p]),
     "les_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "les_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -354,10 +354,12 @@ class Solver:
             _check(rc)
         return stats if check else (rc, stats)
 
-    def forces(self, tri, p, stream=None):
-        out = (C.c_double * 4)()
-        _check(lib().forces(self.handle, _ptr(tri, torch.float32), tri.shape[0], _ptr(p, torch.float64), out,
-                            _stream(stream)))
+    def forces(self, tri, p, u=None, stream=None):
+        """[0:3] pressure force, [3] triangles used, [4:7] viscous force, [7] links used,
+        [8:11] momentum-forcing estimate of the last step, [11] 0."""
+        out = (C.c_double * 12)()
+        _check(lib().forces(self.handle, _ptr(tri, torch.float32), tri.shape[0], _ptr(p, torch.float64),
+                            None if u is None else _ptr(u, self.dtype, "u"), out, _stream(stream)))
         return list(out)
 
     PROFILE_SLOTS = ("csm", "predict", "forcing", "faces", "rhs", "residual", "cg_dir_spmv", "cg_update",

@@ -470,6 +470,7 @@ def test_forces_match_oracle_and_closed_forms(L):
         assert np.allclose(out[:3], ref_out[:3], rtol=1e-10, atol=1e-10 * np.abs(p).max() * R * R)
     out = solver.forces(tt, _t(np.where(inside, 0.0, X.reshape(-1)), torch.float64))
     assert out[0] == pytest.approx(-4.0 / 3.0 * np.pi * R ** 3, rel=0.05)
+    assert out[7] == 0.0
     # dirty soup with non-finite and degenerate triangles: skipped on both sides
     bad = tri.copy()
     bad[3, 0, 0] = np.nan
@@ -546,3 +547,35 @@ def test_surface_pressure_full_size_dirty_sphere_properties(L):
     assert np.allclose(a1[ok], 1.75, rtol=1e-15, atol=0)
     assert np.all(np.isnan(a0) <= np.isnan(a1))          # filtering never adds a side
     assert F1[3] == ok.sum() and F1[3] < F0[3]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_viscous_force_matches_oracle(L, prec):
+    """The cut-link viscous force of forces() against the oracle on a random field with a moving wall,
+    and the sheared-plate closed form F_x = 2 nu a A."""
+    g, geo, ref, solver, u, rng = _setup_ops(L, prec)
+    td = solver.dtype
+    uib = np.zeros((len(ref.rec), 3))
+    uib[:, 1] = 0.25
+    ref.rec["uib"][:] = uib
+    geo.set_boundary_velocity(_t(uib, torch.float64))
+    p = np.zeros(ref.N)
+    out = solver.forces(torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda"), _t(p, torch.float64),
+                        _t(u, td))
+    ref_out = ref.viscous_force(u.astype(np.float64).reshape(-1))
+    assert out[7] == ref_out[3] == len(ref.rec)
+    tol = 1e-12 if prec == 0 else 2e-6
+    assert np.allclose(out[4:7], ref_out[:3], rtol=tol, atol=tol * np.abs(ref_out[:3]).max())
+    # sheared plate across a periodic box
+    nx, ny, nz, nu, a = 8, 6, 9, 0.07, 0.3
+    bc = (0, 0, 0, 0, 3, 3)
+    zw = 4.3
+    tri = np.array([[(-1, -1, zw), (9, -1, zw), (9, 9, zw)], [(-1, -1, zw), (9, 9, zw), (-1, 9, zw)]], np.float32)
+    g2, geo2, ref2 = both_geometries(L, nx, ny, nz, tri, bc, nu, 0.1)
+    solver2 = L.Solver(g2, nu, 0.1, bc, precision=L.FP64, tol=1e-10, geometry=geo2)
+    z = np.arange(nz) + 0.5
+    zz = np.broadcast_to(z[:, None, None], (nz, ny, nx)).reshape(-1)
+    uu = np.concatenate([a * np.abs(zz - float(np.float32(zw))), np.zeros(2 * nx * ny * nz)])
+    out = solver2.forces(torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda"),
+                         _t(np.zeros(nx * ny * nz), torch.float64), _t(uu, torch.float64))
+    assert out[4] == pytest.approx(2 * nu * a * nx * ny, rel=1e-12)

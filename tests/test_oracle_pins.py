@@ -798,3 +798,27 @@ def test_surface_pressure_uniform_and_matches_forces_on_a_clean_body():
     ref = case.forces(tri, p)
     if both.all():
         assert np.allclose(F[:3], ref[:3], rtol=1e-12, atol=1e-12)
+
+
+def test_viscous_force_of_a_sheared_plate():
+    """A zero-thickness no-slip plate spanning a periodic box at z = 4.3 with u_x = a |z - 4.3| on both
+    sides: the ghost values of Eq. q_axis are exact for the linear profiles, every column has one cut
+    link on each side, each carries nu a dx^2, so F_x = 2 nu a (nx ny dx^2) and F_y = F_z = 0; with
+    u_x = a (z - 4.3) (the same shear continuing through the plate) the two sides cancel."""
+    nx, ny, nz, nu, a = 8, 6, 9, 0.07, 0.3
+    case = oracle.Case(nx, ny, nz, nu=nu, dt=0.1, bc=(0, 0, 0, 0, 3, 3))
+    zw = 4.3
+    tri = np.array([[(-1, -1, zw), (9, -1, zw), (9, 9, zw)], [(-1, -1, zw), (9, 9, zw), (-1, 9, zw)]], np.float32)
+    case.set_geometry(tri)
+    assert len(case.rec) == 2 * nx * ny
+    z = np.arange(nz) + 0.5
+    zz = np.broadcast_to(z[:, None, None], (nz, ny, nx)).reshape(-1)
+    zwf = float(np.float32(zw))
+    u = np.concatenate([a * np.abs(zz - zwf), np.zeros(case.N), np.zeros(case.N)])
+    F = case.viscous_force(u)
+    assert F[3] == 2 * nx * ny
+    assert F[0] == pytest.approx(2 * nu * a * nx * ny, rel=1e-12)
+    assert abs(F[1]) < 1e-14 and abs(F[2]) < 1e-14
+    u = np.concatenate([a * (zz - zwf), np.zeros(case.N), np.zeros(case.N)])
+    F = case.viscous_force(u)
+    assert abs(F[0]) < 1e-12
