@@ -179,7 +179,8 @@ int les_predict(les_state* st, const void* d_u, const void* d_U, const void* d_n
                 const void* d_Hprev, void* d_H, void* d_ustar, int32_t first_step, void* stream);
 /* Crank-Nicolson predictor (Eq. crank-nicolson) with U = U^n and nu_t = nu_t(u^n) in both halves:
  * delta = u* - u solves delta - (dt/2) L_0(delta) = dt L(u), L_0 the linear part of L (ghost values
- * without wall and inflow velocities), by BiCGStab over the stacked three components from delta = 0.
+ * without wall and inflow velocities), by BiCGStab over the stacked three components, starting from the
+ * increment of the previous converged call on this state (from 0 on the first call or after a failure).
  * d_H[3N] receives L(u), d_ustar[3N] the predicted field; *iters (host, may be NULL) the iterations.
  * Needs a state created with integrator = IBM_CRANK_NICOLSON.  Synchronises every 4 iterations.
  * Returns IBM_E_NOCONV at mom_max_iter (d_ustar then holds the last iterate), IBM_E_NONFINITE. */

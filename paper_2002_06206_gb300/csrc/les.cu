@@ -758,7 +758,7 @@ template <class T, bool GENERAL>
 __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_begin(Dom D, FaceLayout F, const T* __restrict__ u, const T* __restrict__ U,
                                                   const T* __restrict__ nut, T* __restrict__ H, T* __restrict__ r,
                                                   T* __restrict__ rh, T* __restrict__ x, T nu, T gam, T dt, double tol2,
-                                                  int maxit, SolveScal* sc, double* partials, unsigned* counter,
+                                                  int maxit, int keepx, SolveScal* sc, double* partials, unsigned* counter,
                                                   const int32_t* __restrict__ list, long long nlist) {
     T a0 = 0;
     flux_cells<GENERAL, T>(D, F, u, U, nut, nu, gam, list, nlist, [&](long long P, const T (&h)[3], const T (&uc)[3]) {
@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_begin(
             H[q] = h[c];
             r[q] = b;
             rh[q] = b;
-            x[q] = (T)0;
+            if (!keepx) x[q] = (T)0;
             a0 += b * b;
         }
     });
@@ -808,13 +808,14 @@ __global__ void k_cn_p(long long n, const T* __restrict__ r, T* __restrict__ p, 
 }
 
 // y = M xin = xin - (dt/2) L_0(xin).  mode 0: (w, y) -> alpha = rho / (r_hat, v).  mode 1 (xin = s):
-// (y, s), (y, y) -> omega.
+// (y, s), (y, y) -> omega.  mode 2 (warm start, xin = the previous increment): r = b - M xin with b
+// read from and r written to r2, r_hat = r in y, (r, r) -> rr = rho.
 template <class T, bool GENERAL>
 __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(Dom D, FaceLayout F, const T* __restrict__ xin,
                                                   const T* __restrict__ U, const T* __restrict__ nut,
-                                                  T* __restrict__ y, const T* __restrict__ w, T nu, T gam, T hdt,
-                                                  int mode, SolveScal* sc, double* partials, unsigned* counter,
-                                                  const int32_t* __restrict__ list, long long nlist) {
+                                                  T* __restrict__ y, const T* __restrict__ w, T* r2, T nu, T gam,
+                                                  T hdt, int mode, SolveScal* sc, double* partials,
+                                                  unsigned* counter, const int32_t* __restrict__ list, long long nlist) {
     if (sc->done) return;
     T a0 = 0, a1 = 0;
     flux_cells<GENERAL, T>(D, F, xin, U, nut, nu, gam, list, nlist, [&](long long P, const T (&h)[3], const T (&uc)[3]) {
@@ -823,6 +824,13 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(
             const long long q = c * D.N + P;
             const T xv = uc[c];
             const T yv = xv - hdt * h[c];
+            if (mode == 2) {
+                const T rn = r2[q] - yv;
+                r2[q] = rn;
+                y[q] = rn;
+                a0 += rn * rn;
+                continue;
+            }
             y[q] = yv;
             if (mode == 0) {
                 a0 += w[q] * yv;
@@ -840,6 +848,13 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_cn_apply(
             return;
         }
         const double t0 = t[0] + sc->part[0], t1 = t[1] + sc->part[1];
+        if (mode == 2) {
+            sc->rr = t0;
+            sc->rho = t0;
+            if (!isfinite(t0)) sc->nonfinite = 1;
+            if (!isfinite(t0) || t0 <= sc->target2) sc->done = 1;
+            return;
+        }
         if (mode == 0) {
             sc->rv = t0;
             sc->alpha = t0 != 0.0 ? sc->rho / t0 : 0.0;
@@ -926,19 +941,27 @@ int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T*
     const T nu = (T)c.nu, gam = (T)c.quick, dt = (T)c.dt, hdt = (T)(0.5 * c.dt);
     const unsigned ngen = lin_blocks(c.n_general > 0 ? c.n_general : 1, 256);
     prof_begin(c.prof, PS_PREDICT, s);
+    // warm start from the previous step's increment (the increment changes slowly from step to step)
+    const int keepx = w.have_x;
     k_cn_begin<T, false><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol,
-                                                        w.maxit, w.sc, c.partials, c.counter, nullptr, 0);
+                                                        w.maxit, keepx, w.sc, c.partials, c.counter, nullptr, 0);
     k_cn_begin<T, true><<<ngen, 256, 0, s>>>(c.D, c.F, u, U, nut, H, r, rh, x, nu, gam, dt, w.tol * w.tol, w.maxit,
-                                             w.sc, c.partials, c.counter, c.general, c.n_general);
+                                             keepx, w.sc, c.partials, c.counter, c.general, c.n_general);
     prof_end(c.prof, PS_PREDICT, s);
     IBM_LAUNCHED("k_cn_begin");
     IBM_COUNT(c, 2);
     auto apply = [&](const T* in, T* out, int mode) {
-        k_cn_apply<T, false><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc,
+        const T* wv = mode == 2 ? nullptr : rh;
+        T* r2 = mode == 2 ? r : nullptr;
+        k_cn_apply<T, false><<<tile_grid<T>(c), dim3(FT_X, FT_Y), fast_tile_smem<T>(), s>>>(Dh, c.F, in, U, nut, out, wv, r2, nu, gam, hdt, mode, w.sc,
                                                             c.partials, c.counter, nullptr, 0);
-        k_cn_apply<T, true><<<ngen, 256, 0, s>>>(Dh, c.F, in, U, nut, out, rh, nu, gam, hdt, mode, w.sc, c.partials,
+        k_cn_apply<T, true><<<ngen, 256, 0, s>>>(Dh, c.F, in, U, nut, out, wv, r2, nu, gam, hdt, mode, w.sc, c.partials,
                                                  c.counter, c.general, c.n_general);
     };
+    if (keepx) {
+        apply(x, rh, 2);
+        IBM_COUNT(c, 2);
+    }
     for (;;) {
         prof_begin(c.prof, PS_MOMENTUM, s);
         for (int it = 0; it < 4; ++it) {
@@ -959,6 +982,7 @@ int predict_cn_t(const LesCtx& c, const T* u, const T* U, const T* nut, T* H, T*
     IBM_LAUNCHED("k_cn_finish");
     IBM_COUNT(c, 1);
     if (iters) *iters = w.hsc->iters;
+    w.have_x = !w.hsc->nonfinite && w.hsc->rr <= w.hsc->target2;
     if (w.hsc->nonfinite) return ibm_fail(IBM_E_NONFINITE, "crank-nicolson momentum solve: non-finite residual");
     if (!(w.hsc->rr <= w.hsc->target2))
         return ibm_fail(IBM_E_NOCONV, "crank-nicolson momentum solve: relative residual %.3e after %d iterations",

@@ -59,6 +59,7 @@ struct CNWork {
     SolveScal* hsc;           // pinned host copy
     double tol;
     int maxit;
+    int have_x;               // x holds the last converged increment (the next solve starts from it)
 };
 
 struct LesCtx {
