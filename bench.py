@@ -69,24 +69,27 @@ def read_peaks():
         return FALLBACK_HBM, "fallback"
 
 
-def src_hash():
+def src_hash(files=None):
+    """Hash of the CUDA sources (all of them, or the named files of csrc/)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2002_06206_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files if files is not None else os.listdir(csrc)):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    """DRAM bytes per launch from the committed ncu summary, if the sources that define that kernel
+    (the files listed with it) are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("source_hash") != src_hash():
+        k = d["kernels"].get(kernel_key)
+        if not k or k.get("source_hash") != src_hash(k["files"]):
             return None
-        return d["kernels"].get(kernel_key, {}).get("dram_bytes_per_launch_full_size")
+        return k.get("dram_bytes_per_launch_full_size")
     except Exception:
         return None
 

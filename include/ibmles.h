@@ -71,7 +71,8 @@ typedef struct {
     double inner_tol;    /* FP32 inner solve: relative reduction per FP64 refinement (0 = 1e-4) */
     double sor_omega;    /* over-relaxation factor of red-black SOR (0 = 1.9) */
     int32_t precond;     /* CG preconditioner: 0 none, 1 geometric multigrid V-cycle */
-    int32_t mg_sweeps;   /* red-black Gauss-Seidel sweeps before and after each coarse correction (0 = 2) */
+    int32_t mg_sweeps;   /* red-black Gauss-Seidel sweeps on the fine grid before and after the coarse
+                            correction (0 = 2); the coarse levels take one sweep each way */
     double mg_omega;     /* multigrid coarse-correction factor in (0, 2) (0 = 1.6) */
     double quick;        /* fraction of QUICK in the advected face value, [0, 1] (Sec. 3.1/3.3: 0.05-0.1) */
     int32_t integrator;  /* IBM_ADAMS_BASHFORTH (explicit, Euler first step) or IBM_CRANK_NICOLSON

@@ -489,6 +489,9 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
     const T scale = (T)(c.D.dx * c.D.dx);
     const T om = (T)mg.omega;
     const int S = mg.sweeps;
+    // one sweep before and after on the coarse levels: measured faster overall on the dirty sphere than
+    // S there too (a few more outer iterations, much less coarse-level work)
+    const int SC = S > 0 ? 1 : 0;
     const CellGrid& g = c.cg;
     int launches = 0;
     bool vec = false;
@@ -526,7 +529,7 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
         const int top = tf < mg.nlev ? tf : mg.nlev - 1;
         for (int l = 1; l < top; ++l) {
             const MGLev& L = mg.lev[l];
-            for (int q = 0; q < S; ++q) {
+            for (int q = 0; q < SC; ++q) {
                 k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, q == 0, sc);
                 k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
                 launches += 2;
@@ -539,7 +542,7 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
             for (int l = 0; l < mg.nlev; ++l) M.lev[l] = mg.lev[l];
             M.first = tf;
             M.nlev = mg.nlev;
-            M.sweeps = S;
+            M.sweeps = SC;
             M.coarse_sweeps = mg.coarse_sweeps;
             M.omega = mg.omega;
             cudaLaunchConfig_t cfg = {};
@@ -564,7 +567,7 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
             const MGLev& L = mg.lev[l];
             k_mg_prolong<T><<<lin_blocks(L.N), 256, 0, s>>>(L.N, L.nx, L.ny, (T*)L.x, mg.lev[l + 1], om, sc);
             ++launches;
-            for (int q = 0; q < S; ++q) {
+            for (int q = 0; q < SC; ++q) {
                 k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
                 k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, 0, sc);
                 launches += 2;
