@@ -10,6 +10,11 @@
  * Face fields are concatenated Ux | Uy | Uz with Ux[(nx+1)*ny*nz] (index i + (nx+1)*(j + ny*k),
  * face at x = i*dx), Uy[nx*(ny+1)*nz], Uz[nx*ny*(nz+1)].
  * Triangle soups are float32 [ntri][3 vertices][xyz] in grid units (dx = 1 in the soup).
+ *
+ * Parity unpinned: where the paper is silent the oracle states a reading, and four of them have no
+ * independent check beyond invariants -- the transpose SGS term on cut faces (or_predict,
+ * or_momentum_operator), the placement of the forcing (or_forcing), the dead-end threshold
+ * (or_forcing) and the outer boundary conditions (every operator that reads across a domain face).
  */
 #ifndef IBM_ORACLE_H
 #define IBM_ORACLE_H
