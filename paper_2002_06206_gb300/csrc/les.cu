@@ -95,8 +95,8 @@ __device__ __forceinline__ T face_adv(const Dom& D, const T* __restrict__ u, int
 // L(u) of a cell per unit volume: flux-form advection with the face velocity U (central value
 // blended with QUICK), diffusion with nu + nu_t, the transpose part of the SGS stress divergence.
 // flux_general applies the ghost and boundary rules of vel_across on every link; the tiled fast path
-// evaluates the same formulas for a cell where they reduce to direct reads (fast_cell).  With D.hom set the ghost values
-// lose their wall and inflow velocities, which gives the linear part of L.
+// evaluates the same formulas for a cell where they reduce to direct reads (fast_cell).  With D.hom set
+// the ghost values lose their wall and inflow velocities, which gives the linear part of L.
 
 // The cell and its six neighbours (across periodic seams too) have no cut link: its flux then needs
 // only neighbour values and the domain-boundary ghosts, which the tiles below hold.
@@ -224,71 +224,71 @@ __device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& 
             // k - 3 left; the barrier at the end of the step publishes it
             const bool more = k + 3 <= z1 + 1;
             if (more) fetch(k + 3);
-        const long long P = i + (long long)D.sy * j + D.sz * k;
-        if (i < D.nx && j < D.ny && (D.fast ? D.fast[P] != 0 : fast_cell(D, P, i, j, k))) {
-            const int xc[3] = {i, j, k};
-            const T* S[5];
+            const long long P = i + (long long)D.sy * j + D.sz * k;
+            if (i < D.nx && j < D.ny && (D.fast ? D.fast[P] != 0 : fast_cell(D, P, i, j, k))) {
+                const int xc[3] = {i, j, k};
+                const T* S[5];
 #pragma unroll
-            for (int d = 0; d < 5; ++d) S[d] = sm + slot(k + d - 2) * (FT_NV * FT_PL) + cidx;
-            // value of variable v at (i + dx, j + dy, k + dz)
-            auto V = [&](int v, int dx, int dy, int dz) -> T { return S[dz + 2][v * FT_PL + dy * FT_SX + dx]; };
-            const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-            const T nutP = V(3, 0, 0, 0);
-            T h[3] = {0, 0, 0};
-            T uc[3], un[3][6], GP[3][3];
+                for (int d = 0; d < 5; ++d) S[d] = sm + slot(k + d - 2) * (FT_NV * FT_PL) + cidx;
+                // value of variable v at (i + dx, j + dy, k + dz)
+                auto V = [&](int v, int dx, int dy, int dz) -> T { return S[dz + 2][v * FT_PL + dy * FT_SX + dx]; };
+                const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                const T nutP = V(3, 0, 0, 0);
+                T h[3] = {0, 0, 0};
+                T uc[3], un[3][6], GP[3][3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uc[c] = V(c, 0, 0, 0);
+                for (int c = 0; c < 3; ++c) {
+                    uc[c] = V(c, 0, 0, 0);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    un[c][2 * a] = V(c, -e[a][0], -e[a][1], -e[a][2]);
-                    un[c][2 * a + 1] = V(c, e[a][0], e[a][1], e[a][2]);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int s = -1; s <= 1; s += 2) {
-                    const int lb = 2 * a + (s > 0);
-                    const T Uf = U[F.index(a, i + (a == 0 && s > 0), j + (a == 1 && s > 0), k + (a == 2 && s > 0))];
-                    const int ox = s * e[a][0], oy = s * e[a][1], oz = s * e[a][2];
-                    // a link through a non-periodic domain face
-                    const bool dom = (xc[a] + s < 0 || xc[a] + s >= n[a]) && D.bc[2 * a] != IBM_BC_PERIODIC;
-                    const T nutf = dom ? nutP : (T)0.5 * (nutP + V(3, ox, oy, oz));
-                    T GN[3] = {0, 0, 0};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (q == a) continue;
-                        GN[q] = (V(a, ox + e[q][0], oy + e[q][1], oz + e[q][2]) -
-                                 V(a, ox - e[q][0], oy - e[q][1], oz - e[q][2])) * inv2dx;
+                    for (int a = 0; a < 3; ++a) {
+                        un[c][2 * a] = V(c, -e[a][0], -e[a][1], -e[a][2]);
+                        un[c][2 * a + 1] = V(c, e[a][0], e[a][1], e[a][2]);
                     }
+                }
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const T uP = uc[c], uN = un[c][lb];
-                        const T D1 = (uN - uP) * invdx;
-                        const T Tt = c == a ? D1 : (dom ? (T)s * GP[c][a] : (T)s * (T)0.5 * (GP[c][a] + GN[c]));
-                        T adv = (T)0.5 * (uP + uN);
-                        if (gam != (T)0 && !dom) {
-                            // far upwind: L - e_a for U >= 0 (L = P or P - e_a), R + e_a otherwise
-                            const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
-                            const int fo = Uf >= (T)0 ? (s > 0 ? -1 : -2) : (s > 0 ? 2 : 1);
-                            const T far = V(c, fo * e[a][0], fo * e[a][1], fo * e[a][2]);
-                            const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - far) / (T)8
-                                                   : ((T)6 * uR + (T)3 * uL - far) / (T)8;
-                            adv = ((T)1 - gam) * adv + gam * q;
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int s = -1; s <= 1; s += 2) {
+                        const int lb = 2 * a + (s > 0);
+                        const T Uf = U[F.index(a, i + (a == 0 && s > 0), j + (a == 1 && s > 0), k + (a == 2 && s > 0))];
+                        const int ox = s * e[a][0], oy = s * e[a][1], oz = s * e[a][2];
+                        // a link through a non-periodic domain face
+                        const bool dom = (xc[a] + s < 0 || xc[a] + s >= n[a]) && D.bc[2 * a] != IBM_BC_PERIODIC;
+                        const T nutf = dom ? nutP : (T)0.5 * (nutP + V(3, ox, oy, oz));
+                        T GN[3] = {0, 0, 0};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            if (q == a) continue;
+                            GN[q] = (V(a, ox + e[q][0], oy + e[q][1], oz + e[q][2]) -
+                                     V(a, ox - e[q][0], oy - e[q][1], oz - e[q][2])) * inv2dx;
                         }
-                        const T conv = -(T)s * Uf * adv;
-                        h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
-                    }
-                }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[c] *= invdx;
-            epi(P, h, uc);
-        }
+                        for (int c = 0; c < 3; ++c) {
+                            const T uP = uc[c], uN = un[c][lb];
+                            const T D1 = (uN - uP) * invdx;
+                            const T Tt = c == a ? D1 : (dom ? (T)s * GP[c][a] : (T)s * (T)0.5 * (GP[c][a] + GN[c]));
+                            T adv = (T)0.5 * (uP + uN);
+                            if (gam != (T)0 && !dom) {
+                                // far upwind: L - e_a for U >= 0 (L = P or P - e_a), R + e_a otherwise
+                                const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
+                                const int fo = Uf >= (T)0 ? (s > 0 ? -1 : -2) : (s > 0 ? 2 : 1);
+                                const T far = V(c, fo * e[a][0], fo * e[a][1], fo * e[a][2]);
+                                const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - far) / (T)8
+                                                       : ((T)6 * uR + (T)3 * uL - far) / (T)8;
+                                adv = ((T)1 - gam) * adv + gam * q;
+                            }
+                            const T conv = -(T)s * Uf * adv;
+                            h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
+                        }
+                    }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[c] *= invdx;
+                epi(P, h, uc);
+            }
             if (more) commit(k + 3);
             __syncthreads();
         }
