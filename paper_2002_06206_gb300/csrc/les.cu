@@ -352,11 +352,13 @@ __device__ __forceinline__ void flux_general(const Dom& D, const FaceLayout& F, 
     for (int c = 0; c < 3; ++c) h[c] *= invdx;
 }
 
+// (grids hold fewer than 2^31 cells: 32-bit division)
 __device__ __forceinline__ void cell_coords(const Dom& D, long long P, int& i, int& j, int& k) {
-    k = (int)(P / D.sz);
-    const long long r = P - (long long)k * D.sz;
-    j = (int)(r / D.sy);
-    i = (int)(r - (long long)j * D.sy);
+    const unsigned u = (unsigned)P, sy = (unsigned)D.sy, sz = (unsigned)D.sz;
+    const unsigned kk = u / sz, r = u - kk * sz, jj = r / sy;
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(r - jj * sy);
 }
 
 // Calls body(P, i, j, k) for the entries of the list of the cells that are not fast_cell, strided

@@ -12,12 +12,14 @@ namespace {
 
 // Persistent launch: a fixed number of blocks walks the (x, y, z) tiles of the grid, so that a kernel
 // ending in a grid reduction pays the reduction tail once per block, not once per wave of tiles.
+// Tile indices are 32-bit (a grid has fewer than 2^31 cells): a 64-bit division per tile would cost
+// more than the tile's arithmetic.
 #define X4_TILE_LOOP_BEGIN                                                                      \
-    const int gx_ = (D.nx / 4 + X4_TX - 1) / X4_TX, gy_ = (D.ny + X4_TY - 1) / X4_TY;          \
-    const long long ntiles_ = (long long)gx_ * gy_ * ((D.nz + IBM_KU - 1) / IBM_KU);           \
-    for (long long tile_ = blockIdx.x; tile_ < ntiles_; tile_ += gridDim.x) {                  \
-        const int bx_ = (int)(tile_ % gx_), by_ = (int)((tile_ / gx_) % gy_);                  \
-        const int bz_ = (int)(tile_ / ((long long)gx_ * gy_));                                 \
+    const unsigned gx_ = (D.nx / 4 + X4_TX - 1) / X4_TX, gy_ = (D.ny + X4_TY - 1) / X4_TY;     \
+    const unsigned ntiles_ = gx_ * gy_ * (unsigned)((D.nz + IBM_KU - 1) / IBM_KU);             \
+    for (unsigned tile_ = blockIdx.x; tile_ < ntiles_; tile_ += gridDim.x) {                   \
+        const unsigned r_ = tile_ / gx_;                                                       \
+        const int bx_ = (int)(tile_ - r_ * gx_), by_ = (int)(r_ % gy_), bz_ = (int)(r_ / gy_); \
         const int i0 = 4 * (bx_ * X4_TX + threadIdx.x), j = by_ * X4_TY + threadIdx.y;         \
         const int kb = bz_ * IBM_KU;                                                           \
         const bool active = i0 < D.nx && j < D.ny;
@@ -196,7 +198,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict0_x4(Dom D, const float* __r
     auto zv = [&](long long c) { return z[c]; };
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
          t += (long long)gridDim.x * blockDim.x) {
-        const int xp = (int)(t % px), Y = (int)((t / px) % C.ny), Z = (int)(t / ((long long)px * C.ny));
+        const unsigned tu = (unsigned)t, rq = tu / (unsigned)px;
+        const int xp = (int)(tu - rq * (unsigned)px), Y = (int)(rq % (unsigned)C.ny), Z = (int)(rq / (unsigned)C.ny);
         const int i0 = 4 * xp;
         float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
