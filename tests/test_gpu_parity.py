@@ -579,3 +579,40 @@ def test_viscous_force_matches_oracle(L, prec):
     out = solver2.forces(torch.zeros((0, 3, 3), dtype=torch.float32, device="cuda"),
                          _t(np.zeros(nx * ny * nz), torch.float64), _t(uu, torch.float64))
     assert out[4] == pytest.approx(2 * nu * a * nx * ny, rel=1e-12)
+
+
+@pytest.fixture(scope="module")
+def oracle_drag_history():
+    """Pressure drag coefficient of the oracle's sphere run (64x32x32, Re = 100, FP64), steps 26-50."""
+    cfg = W.get_config("sphere_64x32x32")
+    tri = cfg.soup()
+    ref = oracle.Case(cfg.nx, cfg.ny, cfg.nz, 1.0, cfg.nu, cfg.dt, cfg.bc)
+    ref.set_geometry(tri)
+    ost = ref.initial_state(W.initial_fields(cfg))
+    cd = []
+    for n in range(50):
+        ref.step(ost, tol=1e-10)
+        if n >= 25:
+            cd.append(ref.forces(tri, ost["p"])[0] / (0.5 * cfg.a_ref))
+    return np.array(cd)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_time_averaged_drag_matches_oracle(L, prec, tol, oracle_drag_history):
+    """Sphere D = 8 at Re = 100 (64x32x32): 50 steps on the GPU and in the FP64 oracle, pressure drag
+    coefficient Cd = F_x / (U^2 A / 2) from the Shepard surface integral after every step, averaged over
+    steps 26-50.  FP64 and the FP32 + FP64-refinement mode agree with the oracle within 1 %."""
+    cfg = W.get_config("sphere_64x32x32")
+    tri = cfg.soup()
+    g, geo, ref = both_geometries(L, cfg.nx, cfg.ny, cfg.nz, tri, cfg.bc, cfg.nu, cfg.dt)
+    solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, precision=prec, tol=tol, geometry=geo, precond=L.MULTIGRID)
+    st = solver.fields(W.initial_fields(cfg))
+    tt = torch.from_numpy(tri).cuda()
+    cd = []
+    for n in range(50):
+        solver.step(st)
+        if n >= 25:
+            cd.append(solver.forces(tt, st["p"])[0] / (0.5 * cfg.a_ref))
+    a, b = float(np.mean(cd)), float(np.mean(oracle_drag_history))
+    assert abs(b) > 0.1
+    assert abs(a - b) <= 0.01 * abs(b), (a, b)
