@@ -383,7 +383,8 @@ def run_ours(args):
     solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=cfg.precision, solver=L.CG, tol=cfg.tol,
                       max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
                       csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond,
-                      quick=args.quick, integrator=integ, mg_sweeps=args.mg_sweeps)
+                      quick=args.quick, integrator=integ, mg_sweeps=args.mg_sweeps,
+                      mg_omega=args.mg_omega)
     st = solver.fields(W.initial_fields(cfg))
     for _ in range(args.warmup):
         solver.step(st)
@@ -499,6 +500,7 @@ def run_ours(args):
                        "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol,
                        "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
                        "quick": args.quick, "mg_sweeps": args.mg_sweeps if precond else None,
+                       "mg_omega": args.mg_omega if precond else None,
                        "momentum_bicgstab_iters_per_step": M,
                        "timed_steps": [args.warmup + 1, args.warmup + args.steps],
                        "parallelism": "replicas" if world > 1 else "single",
@@ -542,6 +544,7 @@ def main():
                     help="Crank-Nicolson (the paper's production integrator) or Adams-Bashforth 2")
     ap.add_argument("--quick", type=float, default=0.1, help="QUICK fraction of the advected face value")
     ap.add_argument("--mg-sweeps", type=int, default=2, help="red-black sweeps before and after each coarse correction")
+    ap.add_argument("--mg-omega", type=float, default=1.8, help="multigrid coarse-correction factor")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
