@@ -1,10 +1,11 @@
 // les.cu -- the per-step stencil kernels of the immersed-boundary LES (Sec. 2.1-2.4): CSM eddy
-// viscosity, AB2 momentum predictor, distributed direct forcing, face velocities, Poisson right-hand
-// side, velocity correction, and the Shepard surface force.
+// viscosity, the momentum flux with the QUICK hybrid and its two predictors (Crank-Nicolson with a
+// BiCGStab momentum solve, Adams-Bashforth 2), distributed direct forcing, face velocities, Poisson
+// right-hand side, velocity correction, and the Shepard surface and viscous forces.
 //
-// All cell kernels use the same launch shape: a 32 x 8 thread tile over (x, y), each thread marching
-// along z over a chunk of planes, so consecutive threads touch consecutive cells (coalesced rows) and
-// the y/z neighbours of a tile are re-read from L1/L2 rather than HBM.
+// Cell kernels use a 32 x 8 thread tile over (x, y) so that consecutive threads touch consecutive
+// cells (coalesced rows); the momentum flux walks z-marching tiles staged in shared memory, with the
+// cells next to cut links in a separate general kernel.
 #include "solver.cuh"
 
 #ifndef IBM_FLUX_MINB
