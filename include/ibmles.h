@@ -148,7 +148,12 @@ int ibm_geom_info(const ibm_geom* geom, int64_t* n_rec, int64_t* n_inc);
  * d/dx, c_ib, c_p, c_o, w_near, w_far; d_cellrec[N] = first record of each cell or -1. */
 int ibm_geom_export(const ibm_geom* geom, int64_t* d_idx, double* d_coef, int64_t* d_cellrec,
                     void* stream);
-/* Wall velocity u_IB per record (d_uib[n_rec][3], double); NULL resets it to zero. */
+/* Wall velocity u_IB (Eq. forcing_term) per record, d_uib[n_rec][3] in FP64 in record order, copied
+ * on `stream`; NULL resets it to zero.  It enters the ghost values of Eq. q_axis, the forcing target,
+ * and the flux of each cut face: the mean of u_IB.e_a over the face's two records.  A nonzero value
+ * therefore lets fluid cross the wall at the wall's own velocity, as in the prescribed-velocity
+ * Taylor-Green verification of Sec. 2.5.  The cut faces of a sealed pocket must then carry zero net
+ * flux, or its Poisson block has no solution and the solve ends with IBM_E_NOCONV. */
 int ibm_set_boundary_velocity(ibm_geom* geom, const double* d_uib, void* stream);
 void ibm_geom_destroy(ibm_geom* geom);
 

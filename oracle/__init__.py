@@ -81,7 +81,7 @@ def lib():
         L.or_predict_cn.restype = C.c_int
         L.or_predict_cn.argtypes = [P, P, P, P, P, P, P, P, P, P, C.c_double, C.c_int32]
         L.or_forcing.argtypes = [P, P, P, P, i64, P, P, P]
-        L.or_faces.argtypes = [P, P, P, P, P]
+        L.or_faces.argtypes = [P, P, P, P, P, P, P]
         L.or_rhs.argtypes = [P, P, P, P]
         L.or_apply.argtypes = [P, P, P, P, P]
         L.or_solve.restype = C.c_int
@@ -236,7 +236,8 @@ class Case:
     def faces(self, ustar):
         ustar = np.ascontiguousarray(ustar, np.float64)
         U = np.zeros(self.NF)
-        lib().or_faces(C.byref(self.g), C.byref(self.pr), _p(self.flags), _p(ustar), _p(U))
+        lib().or_faces(C.byref(self.g), C.byref(self.pr), _p(self.flags), _p(self.rec), _p(self.cellrec),
+                       _p(ustar), _p(U))
         return U
 
     def rhs(self, Ustar):

@@ -646,12 +646,26 @@ void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, con
 /* ------------------------------------------------------------------------------------------------ */
 /* Face velocities of the intermediate field (the interface velocity U of Sec. 2.1).                 */
 /* Reading (Rhie-Chow, the paper gives no formula): U*_f is the average of the two cell values on    */
-/* uncut interior faces, zero on cut faces (stationary walls, so every enclosed pocket is consistent),*/
-/* the boundary value on inflow/wall faces and the adjacent cell value on outflow faces, which are    */
-/* then shifted uniformly so that the net boundary flux is zero.                                     */
+/* uncut interior faces, the boundary value on inflow/wall faces and the adjacent cell value on       */
+/* outflow faces, which are then shifted uniformly so that the net boundary flux is zero.             */
+/* Reading (cut faces): the wall's own normal velocity, the mean of u_IB.e_a over the face's two link */
+/* records (one per side; a side without a record is left out).  It is zero for a stationary body,   */
+/* so every sealed pocket's right-hand side sums to zero.  With a prescribed wall velocity, as in the */
+/* Taylor-Green verification of Sec. 2.5, fluid crosses the wall at that velocity.                   */
 
-void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* ustar,
-              double* Ustar) {
+static double cut_face_velocity(const uint8_t* flags, const or_record* rec, const int64_t* cellrec,
+                                int64_t L, int64_t R, int a) {
+    double sum = link_record(flags, rec, cellrec, L, a, +1)->uib[a];
+    double n = 1.0;
+    if (is_cut(flags, R, a, -1)) {
+        sum += link_record(flags, rec, cellrec, R, a, -1)->uib[a];
+        n = 2.0;
+    }
+    return sum / n;
+}
+
+void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+              const int64_t* cellrec, const double* ustar, double* Ustar) {
     const int64_t N = ncells(g);
     double phi_other = 0.0, phi_out = 0.0;
     int64_t n_out = 0;
@@ -668,7 +682,8 @@ void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const
                         int64_t xl[3] = {x[0], x[1], x[2]};
                         xl[a] = f - 1;
                         int64_t L = cell_at(g, xl), R = cell_at(g, x);
-                        Ustar[fi] = is_cut(flags, L, a, +1) ? 0.0 : 0.5 * (ustar[a * N + L] + ustar[a * N + R]);
+                        Ustar[fi] = is_cut(flags, L, a, +1) ? cut_face_velocity(flags, rec, cellrec, L, R, a)
+                                                            : 0.5 * (ustar[a * N + L] + ustar[a * N + R]);
                         continue;
                     }
                     int s = f == 0 ? -1 : +1;
@@ -956,7 +971,7 @@ int or_step(const or_grid* g, const or_params* pr, const uint8_t* flags, const o
         or_forcing(g, pr, flags, rec, nrec, us, us2, st->fsum);
         memcpy(us, us2, (size_t)(3 * N) * sizeof(double));
     }
-    or_faces(g, pr, flags, us, Us);
+    or_faces(g, pr, flags, rec, cellrec, us, Us);
     or_rhs(g, pr, Us, b);
     int status = or_solve(g, pr, flags, b, p, tol, maxit, solver, omega, st);
     or_correct(g, pr, flags, us, Us, p, u, U);

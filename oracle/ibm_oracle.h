@@ -109,8 +109,8 @@ int or_predict_cn(const or_grid* g, const or_params* pr, const uint8_t* flags, c
                   double* ustar, double tol, int32_t maxit);
 void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 int64_t nrec, const double* ustar_in, double* ustar_out, double fsum[3]);
-void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* ustar,
-              double* Ustar);
+void or_faces(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
+              const int64_t* cellrec, const double* ustar, double* Ustar);
 void or_rhs(const or_grid* g, const or_params* pr, const double* Ustar, double* b);
 void or_apply(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* p, double* Ap);
 int or_solve(const or_grid* g, const or_params* pr, const uint8_t* flags, const double* b, double* p,

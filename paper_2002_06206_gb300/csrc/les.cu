@@ -484,7 +484,22 @@ __device__ __forceinline__ long long cell_of(const Dom& D, const int x[3]) {
     return x[0] + (long long)D.sy * x[1] + D.sz * x[2];
 }
 
-// Face velocity of the intermediate field on the faces of axis a.
+// Normal velocity of the wall on a cut face between cells L and R along a: the mean of u_IB.e_a over
+// the face's link records (L's +a record and, when present, R's -a record), in FP64.
+__device__ __forceinline__ double cut_face_velocity(const Dom& D, long long L, long long R, int a) {
+    const unsigned fL = D.flags[L], fR = D.flags[R];
+    double sum = link_record(D, L, fL, 2 * a + 1).uib[a];
+    double n = 1.0;
+    if ((fR >> (2 * a)) & 1u) {
+        sum += link_record(D, R, fR, 2 * a).uib[a];
+        n = 2.0;
+    }
+    return sum / n;
+}
+
+// Face velocity of the intermediate field on the faces of axis a: the mean of the two cell values on
+// uncut interior faces, the wall's normal velocity on cut faces (zero for a stationary body), the
+// boundary value on domain faces.
 template <class T>
 __global__ void k_faces(Dom D, FaceLayout F, int a, const T* __restrict__ us, T* __restrict__ Us) {
     const long long nf = (long long)F.dim[a][0] * F.dim[a][1] * F.dim[a][2];
@@ -498,7 +513,7 @@ __global__ void k_faces(Dom D, FaceLayout F, int a, const T* __restrict__ us, T*
         if (f > 0 && f < na) {
             const long long R = cell_of(D, x), L = R - st;
             const bool cut = D.flags && ((D.flags[L] >> (2 * a + 1)) & 1u);
-            v = cut ? (T)0 : (T)0.5 * (us[a * D.N + L] + us[a * D.N + R]);
+            v = cut ? (T)cut_face_velocity(D, L, R, a) : (T)0.5 * (us[a * D.N + L] + us[a * D.N + R]);
         } else {
             const int s = f == 0 ? -1 : 1;
             const int bc = D.bc[2 * a + (s > 0)];

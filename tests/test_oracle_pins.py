@@ -426,7 +426,7 @@ def test_projection_identity_and_mass_balance():
     Ux, Uy, Uz = oracle.split_faces(r["Us"], 32, 16, 16)
     assert abs(Ux[:, :, 0].sum() - Ux[:, :, -1].sum()) < 1e-12 * Ux[:, :, 0].size
     assert np.all(Uy[:, 0] == 0) and np.all(Uy[:, -1] == 0)
-    # cut faces carry no flux
+    # the cut faces of a stationary wall carry no flux
     fid = case.cut[0]
     N = case.N
     for f in fid[:50]:
@@ -435,6 +435,41 @@ def test_projection_identity_and_mass_balance():
         j, i = divmod(rem, 32)
         face = (Ux[k, j, i + 1], Uy[k, j + 1, i], Uz[k + 1, j, i])[a]
         assert face == 0.0
+
+
+def record_points(case, dx=1.0, lo=0.0):
+    """Physical position X of each link record's wall point: the cell centre moved by d along the
+    record's axis towards its side."""
+    r = case.rec
+    P = r["cell"]
+    X = np.stack([P % case.nx, (P // case.nx) % case.ny, P // (case.nx * case.ny)], 1) + 0.5
+    X[np.arange(len(r)), r["axis"]] += r["side"] * r["d"]
+    return lo + X * dx
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_wall_moving_with_a_uniform_flow_is_invisible(integrator):
+    """A wall carried along by a uniform flow (u_IB = u everywhere) must leave the flow exactly uniform:
+    every ghost of Eq. q_axis reproduces a constant, the forcing sees u*_X = u_IB, and the cut faces
+    pass the wall's own normal velocity, so b = 0 and p stays uniform.  Blocking the cut faces instead
+    would stop the flow at the wall."""
+    n = (12, 10, 8)
+    case = oracle.Case(*n, nu=0.05, dt=0.2, bc=PER, quick=0.1, integrator=integrator)
+    lo, hi = -20.0, 40.0
+    case.set_geometry(np.array([[[3.3, lo, lo], [11.9, hi, lo], [2.6, lo, hi]],
+                                [[2.6, lo, hi], [11.9, hi, lo], [10.8, hi, hi]]], np.float32))
+    assert len(case.rec) > 0 and len(set(case.rec["axis"])) == 3
+    v = np.array([0.7, -0.2, 0.3])
+    case.rec["uib"][:] = v
+    u0 = np.broadcast_to(v[:, None], (3, case.N)).copy()
+    st = case.initial_state(u0)
+    for _ in range(3):
+        s = case.step(st, tol=1e-12)
+        assert s.status == 0
+    assert np.abs(st["u"].reshape(3, -1) - v[:, None]).max() < 1e-12
+    assert np.abs(st["p"] - st["p"].mean()).max() < 1e-10
+    Ux, Uy, Uz = oracle.split_faces(st["U"], *n)
+    assert np.allclose(Ux, v[0], atol=1e-12) and np.allclose(Uy, v[1], atol=1e-12) and np.allclose(Uz, v[2], atol=1e-12)
 
 
 def test_step_conserves_momentum_periodic():

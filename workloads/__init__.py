@@ -5,9 +5,9 @@ flow fields.  It holds none of the method's arithmetic (no classification, no st
 so that the oracle and the CUDA path stay independent of each other.
 """
 from .soups import (icosphere, axis_box, dirty_sphere, cube_and_plate, vehicle_assembly,
-                    fan_disk, random_soup)
-from .configs import CONFIGS, Config, get_config, initial_fields, taylor_green
+                    fan_disk, random_soup, prism_2d, taylor_green_body)
+from .configs import CONFIGS, Config, get_config, initial_fields, taylor_green, taylor_green_velocity
 
 __all__ = ["icosphere", "axis_box", "dirty_sphere", "cube_and_plate", "vehicle_assembly",
            "fan_disk", "random_soup", "CONFIGS", "Config", "get_config", "initial_fields",
-           "taylor_green"]
+           "taylor_green", "prism_2d", "taylor_green_body", "taylor_green_velocity"]

@@ -88,6 +88,15 @@ def initial_fields(cfg, dtype=np.float64, seed=None):
     return u.astype(dtype)
 
 
+def taylor_green_velocity(x, y, t, re):
+    """Analytic Taylor-Green velocity of Sec. 2.5 at physical points (x, y); returns [..., 3]."""
+    f = np.exp(-2.0 * np.pi ** 2 * t / re)
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    return np.stack([-np.cos(np.pi * x) * np.sin(np.pi * y) * f, np.sin(np.pi * x) * np.cos(np.pi * y) * f,
+                     np.zeros_like(x)], -1)
+
+
 def taylor_green(n, t, re, nz=1, lo=-2.0, hi=2.0):
     """Analytic 2-D Taylor-Green vortex of Sec. 2.5 sampled at cell centres of an n x n x nz grid on
     [lo, hi]^2 (periodic); returns (u[3,nz,n,n], p[nz,n,n], dx)."""

@@ -114,6 +114,41 @@ def _cylinder(center, radius, length, axis, nseg, nlen):
     return np.concatenate([side] + caps, 0)
 
 
+def prism_2d(polygon, z_lo, z_hi, dtype=F32):
+    """Open lateral surface of a prism along z over a closed polygon [(x, y), ...] (first point
+    repeated at the end): two triangles per edge, no caps.  Extending it past both z faces of a grid
+    gives a 2-D body for quasi-two-dimensional runs."""
+    P = np.asarray(polygon, np.float64)
+    tri = []
+    for a, b in zip(P[:-1], P[1:]):
+        A0, B0 = [a[0], a[1], z_lo], [b[0], b[1], z_lo]
+        A1, B1 = [a[0], a[1], z_hi], [b[0], b[1], z_hi]
+        tri.append([A0, B0, B1])
+        tri.append([A0, B1, A1])
+    return np.array(tri).astype(dtype)
+
+
+def taylor_green_body(n, nz, shape="circle", lo=-2.0, hi=2.0, nseg=256):
+    """The immersed bodies of the Taylor-Green verification (Sec. 2.5) in grid units of an n x n x nz
+    grid on [lo, hi]^2: a circle of radius 1 ("circle", nseg edges) or the square of side sqrt(2)
+    inscribed in it, turned 45 degrees ("diamond", corners on the axes, 8 edges per side), both
+    centred at the origin and extended 3 cells past the z faces."""
+    dx = (hi - lo) / n
+    c = np.array([-lo / dx, -lo / dx])
+    r = 1.0 / dx
+    if shape == "circle":
+        th = np.linspace(0.0, 2.0 * np.pi, nseg + 1)
+        poly = c + r * np.stack([np.cos(th), np.sin(th)], 1)
+    elif shape == "diamond":
+        corners = np.array([[r, 0.0], [0.0, r], [-r, 0.0], [0.0, -r], [r, 0.0]])
+        s = np.linspace(0.0, 1.0, 9)[:-1]
+        poly = np.concatenate([a + s[:, None] * (b - a) for a, b in zip(corners[:-1], corners[1:])]
+                              + [corners[-1:]]) + c
+    else:
+        raise ValueError(shape)
+    return prism_2d(poly, -3.0, nz + 3.0)
+
+
 def _rot_y(tri, angle_deg, pivot):
     a = np.deg2rad(angle_deg)
     R = np.array([[np.cos(a), 0.0, np.sin(a)], [0.0, 1.0, 0.0], [-np.sin(a), 0.0, np.cos(a)]])
