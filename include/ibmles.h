@@ -145,7 +145,7 @@ int ibm_setup(const ibm_grid* grid, const ibm_geom_params* gp, uint8_t* d_flags,
               ibm_geom** out, void* stream);
 int ibm_geom_info(const ibm_geom* geom, int64_t* n_rec, int64_t* n_inc);
 /* Copy the records out: d_idx[n_rec][6] = cell, far, opp, axis, side, branch; d_coef[n_rec][6] =
- * d/dx, c_ib, c_p, c_o, w_near, w_far; d_cellrec[N] = first record of each cell or -1. */
+ * d/dx, c_ib, c_p, c_o, w_fluid, w_ghost; d_cellrec[N] = first record of each cell or -1. */
 int ibm_geom_export(const ibm_geom* geom, int64_t* d_idx, double* d_coef, int64_t* d_cellrec,
                     void* stream);
 /* Wall velocity u_IB (Eq. forcing_term) per record, d_uib[n_rec][3] in FP64 in record order, copied

@@ -22,7 +22,7 @@ BICGSTAB, CG, RBSOR = 0, 1, 2
 RECORD_DTYPE = np.dtype([
     ("cell", np.int64), ("far", np.int64), ("opp", np.int64), ("axis", np.int64),
     ("side", np.int64), ("branch", np.int64), ("d", np.float64), ("c_ib", np.float64),
-    ("c_p", np.float64), ("c_o", np.float64), ("w_near", np.float64), ("w_far", np.float64),
+    ("c_p", np.float64), ("c_o", np.float64), ("w_fluid", np.float64), ("w_ghost", np.float64),
     ("uib", np.float64, (3,)),
 ])
 

@@ -347,9 +347,9 @@ int64_t or_setup(const or_grid* g, uint8_t* flags, const int64_t* face_id, const
                 r->c_p = -1.0;
                 r->c_o = 0.0;
             }
-            /* Eq. distribution_function with d the near cell's distance (reading). */
-            r->w_near = d / (1.0 + d);
-            r->w_far = (1.0 - d) / (1.0 + d);
+            /* Eq. distribution_function at the near cell's distance d: fluid and ghost branch. */
+            r->w_fluid = d / (1.0 + d);
+            r->w_ghost = (1.0 - d) / (1.0 + d);
             r->uib[0] = r->uib[1] = r->uib[2] = 0.0;
         }
     }
@@ -607,10 +607,15 @@ int or_predict_cn(const or_grid* g, const or_params* pr, const uint8_t* flags, c
 /* ------------------------------------------------------------------------------------------------ */
 /* Distributed direct forcing: Eq. forcing_term, Eq. discrete_forcing_term, Eq. distribution_function,*/
 /* dead-end filter Eq. deadend_filter.  Reading: the velocity at the intersection X is the linear     */
-/* interpolant of the background u* between P and the cell G behind the wall; the force             */
-/* (u_IB - u*_X)/dt is spread with the fluid-side weight d/(dx + d) to P.  The ghost-side weight acts */
-/* on the ghost cell of P's dummy stencil, whose value Eq. q_axis already fixes; G itself belongs to  */
-/* another fluid region and is forced through its own records.  All records use the background u*.  */
+/* interpolant of the background u* between P and the cell G behind the wall, and the force          */
+/* (u_IB - u*_X)/dt is spread to P with the ghost branch of D, (dx - d)/(dx + d).  Three facts give    */
+/* this reading.  P is a ghost cell of the dummy stencil of the cell across the wall.  At d = 0 the   */
+/* weight is 1, so P lands on u_IB exactly: Gibou's imposition, which the paper says D follows.  And  */
+/* P's push stays in proportion to its share (1 - d/dx) of u*_X, so every push also corrects u*_X.    */
+/* The fluid branch d/(dx + d) lacks that last property: at d -> dx it pushes P by half the mismatch  */
+/* while P no longer enters u*_X, and on the Taylor-Green case of Sec. 2.5 with a wall through cell   */
+/* centres that drift grows without bound.  G is forced through its own records.  All records use the */
+/* background u*.                                                                                   */
 
 void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, const or_record* rec,
                 int64_t nrec, const double* ustar_in, double* ustar_out, double fsum[3]) {
@@ -623,11 +628,11 @@ void or_forcing(const or_grid* g, const or_params* pr, const uint8_t* flags, con
         const or_record* R = &rec[r];
         int64_t P = R->cell, G = R->far;
         int dead_P = pr->deadend_on && popcount6(flags[P] & 63) >= 5;
-        if (!dead_P) wsum[P] += R->w_near;
+        if (!dead_P) wsum[P] += R->w_ghost;
         for (int i = 0; i < 3; ++i) {
             double uX = (1.0 - R->d) * ustar_in[i * N + P] + R->d * ustar_in[i * N + G];
             double F = (R->uib[i] - uX) / dt;
-            if (!dead_P) delta[i * N + P] += dt * R->w_near * F;
+            if (!dead_P) delta[i * N + P] += dt * R->w_ghost * F;
         }
     }
     /* Reading: a cell crossed by several IB points receives the sum of their spread forces; where the

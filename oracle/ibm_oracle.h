@@ -11,10 +11,11 @@
  * face at x = i*dx), Uy[nx*(ny+1)*nz], Uz[nx*ny*(nz+1)].
  * Triangle soups are float32 [ntri][3 vertices][xyz] in grid units (dx = 1 in the soup).
  *
- * Parity unpinned: where the paper is silent the oracle states a reading, and four of them have no
+ * Parity unpinned: where the paper is silent the oracle states a reading, and three of them have no
  * independent check beyond invariants -- the transpose SGS term on cut faces (or_predict,
- * or_momentum_operator), the placement of the forcing (or_forcing), the dead-end threshold
- * (or_forcing) and the outer boundary conditions (every operator that reads across a domain face).
+ * or_momentum_operator), the dead-end threshold (or_forcing) and the outer boundary conditions
+ * (every operator that reads across a domain face).  The placement of the forcing (or_forcing) is
+ * pinned by its d = 0 limit and by the Taylor-Green convergence of Sec. 2.5.
  */
 #ifndef IBM_ORACLE_H
 #define IBM_ORACLE_H
@@ -55,7 +56,7 @@ typedef struct {
     int64_t branch;  /* 0 = A (d >= 1/2), 1 = B (d < 1/2, O usable), 2 = C (d < 1/2, O unusable) */
     double d;        /* wall distance from P's centre along the link, in units of dx */
     double c_ib, c_p, c_o;   /* ghost = c_ib*q_IB + c_p*q_P + c_o*q_O */
-    double w_near, w_far;    /* distribution-function weights D for P and G */
+    double w_fluid, w_ghost;    /* Eq. distribution_function at d: fluid branch, ghost branch */
     double uib[3];           /* wall velocity at the intersection (0 for stationary bodies) */
 } or_record;
 

@@ -404,8 +404,8 @@ __global__ void k_build_records(int nx, int ny, int nz, const uint8_t* __restric
                 r.c_o = 0.0;
             }
             const double den = __dadd_rn(1.0, d);
-            r.w_near = __ddiv_rn(d, den);
-            r.w_far = __ddiv_rn(__dsub_rn(1.0, d), den);
+            r.w_fluid = __ddiv_rn(d, den);
+            r.w_ghost = __ddiv_rn(__dsub_rn(1.0, d), den);
             r.uib[0] = r.uib[1] = r.uib[2] = 0.0;
             rec[k++] = r;
         }
@@ -429,8 +429,8 @@ __global__ void k_export(const LinkRec* __restrict__ rec, long long n, int64_t* 
             coef[6 * q + 1] = r.c_ib;
             coef[6 * q + 2] = r.c_p;
             coef[6 * q + 3] = r.c_o;
-            coef[6 * q + 4] = r.w_near;
-            coef[6 * q + 5] = r.w_far;
+            coef[6 * q + 4] = r.w_fluid;
+            coef[6 * q + 5] = r.w_ghost;
         }
     }
 }

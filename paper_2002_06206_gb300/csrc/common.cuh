@@ -17,7 +17,7 @@ struct LinkRec {
     int8_t axis, side, branch, pad;
     double d;          // wall distance from P along the link, in units of dx
     double c_ib, c_p, c_o;
-    double w_near, w_far;
+    double w_fluid, w_ghost;  // Eq. distribution_function at d: fluid branch, ghost branch (forcing)
     double uib[3];
 };
 

@@ -419,8 +419,9 @@ __global__ void __launch_bounds__(256, (FluxOcc<T, GENERAL>::value)) k_predict(D
 
 // Distributed direct forcing (Eq. forcing_term, Eq. discrete_forcing_term), gathered per Omega_inc
 // cell over its own link records: the velocity at the wall point X is interpolated between the cell
-// and the cell behind the wall, the force (u_IB - u_X)/dt is spread to the cell with the fluid-side
-// weight of Eq. distribution_function, and a cell whose weights add up to more than 1 takes their
+// and the cell behind the wall, the force (u_IB - u_X)/dt is spread to the cell with the ghost branch
+// (dx - d)/(dx + d) of Eq. distribution_function (the cell is a ghost of the stencil across the wall;
+// weight 1 at d = 0 puts it on u_IB), and a cell whose weights add up to more than 1 takes their
 // normalised sum.  All reads use the unforced u*, so the result does not depend on thread order.
 template <class T>
 __global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __restrict__ inc, long long n_inc,
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(256) k_forcing_gather(Dom D, const int32_t* __
                 if (!((fl >> bit) & 1u)) continue;
                 const LinkRec& r = link_record(D, X, fl, bit);
                 const long long G = r.far;
-                const T d = (T)r.d, wn = (T)r.w_near;
+                const T d = (T)r.d, wn = (T)r.w_ghost;
                 wsum += wn;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {

@@ -60,7 +60,7 @@ def assert_geometry_equal(geo, ref):
     for q, name in enumerate(("cell", "far", "opp", "axis", "side", "branch")):
         assert np.array_equal(gi[:, q], r[name]), name
     gc = coef.cpu().numpy()
-    for q, name in enumerate(("d", "c_ib", "c_p", "c_o", "w_near", "w_far")):
+    for q, name in enumerate(("d", "c_ib", "c_p", "c_o", "w_fluid", "w_ghost")):
         assert np.array_equal(gc[:, q], r[name]), name
     assert np.array_equal(cellrec.cpu().numpy(), ref.cellrec)
 
