@@ -195,11 +195,14 @@ int les_predict_cn(les_state* st, const void* d_u, const void* d_U, const void* 
 /* Eq. forcing_term + Eq. discrete_forcing_term: in-place forcing of d_ustar; fsum (host, may be
  * NULL, synchronises) = momentum added, sum of du * dx^3. */
 int les_forcing(les_state* st, void* d_ustar, double* fsum, void* stream);
-/* Face velocities U* of the intermediate field, outflow faces shifted to zero net boundary flux. */
+/* Face velocities U* of the intermediate field: the mean of the two cells on uncut interior faces, the
+ * wall's normal velocity on cut faces (see ibm_set_boundary_velocity; 0 for a stationary body), the
+ * boundary value on domain faces, outflow faces shifted to zero net boundary flux. */
 int les_faces(les_state* st, const void* d_ustar, void* d_Ustar, void* stream);
 /* Eq. poisson right-hand side b = div(U*)/dt (double). */
 int les_rhs(les_state* st, const void* d_Ustar, double* d_b, void* stream);
-/* Eq. correction: cell velocity from the central pressure gradient, face velocity from the compact one. */
+/* Eq. correction: cell velocity from the central pressure gradient, face velocity from the compact one
+ * on uncut interior faces; cut faces and wall/inflow faces keep their U* value. */
 int les_correct(les_state* st, const void* d_ustar, const void* d_Ustar, const double* d_p,
                 void* d_u, void* d_U, void* stream);
 
