@@ -311,6 +311,32 @@ def test_predictor_conserves_momentum_periodic():
     assert np.all(np.abs(Hs) < 1e-11 * np.abs(H).sum())
 
 
+def test_viscous_and_sgs_stress_of_a_linear_field_vanish_at_a_wall():
+    """Sec. 2.1 / Eq. SGSstress: for a linear velocity u = c + A x with constant nu and nu_t the stress
+    divergence div(nu grad u + nu_t (grad u + grad u^T)) is zero.  With the face velocities set to zero
+    (no advection) and u_IB = u(X) on every record, the momentum operator must vanish in every cell
+    whose stencil stays inside the box, the cells next to an oblique wall included.  There the ghost
+    values of Eq. q_axis are exact for linear fields, and the transpose term on a cut face takes the
+    cell's own gradient (reading).  Dropping that term, or flipping its sign, leaves 0.04-0.08."""
+    n = (14, 12, 10)
+    case = oracle.Case(*n, nu=0.05, dt=0.2, bc=SLIPBOX)
+    lo, hi = -20.0, 40.0
+    case.set_geometry(np.array([[[5.3, lo, lo], [9.9, hi, lo], [4.1, lo, hi]],
+                                [[4.1, lo, hi], [9.9, hi, lo], [8.7, hi, hi]]], np.float32))
+    A = np.array([[0.3, 0.5, -0.2], [0.1, -0.1, 0.4], [0.25, -0.3, -0.2]])
+    c0 = np.array([0.4, -0.2, 0.1])
+    N = case.N
+    xc = np.stack([np.arange(N) % n[0], (np.arange(N) // n[0]) % n[1], np.arange(N) // (n[0] * n[1])], 1) + 0.5
+    u = (c0[None, :] + xc @ A.T).T.reshape(-1).copy()
+    case.rec["uib"][:] = c0[None, :] + record_points(case) @ A.T
+    assert np.all(case.rec["branch"] < 2) and len(set(case.rec["axis"])) == 3
+    L = case.momentum_operator(u, np.zeros(case.NF), np.full(N, 0.07)).reshape(3, -1)
+    inner = np.all((xc > 3) & (xc < np.array(n) - 3), axis=1)
+    near = inner & ((case.flags & 63) != 0)
+    assert near.sum() >= 40
+    assert np.abs(L[:, inner]).max() < 1e-13
+
+
 def test_predictor_uniform_flow_is_steady():
     n = 6
     case = oracle.Case(n, n, n, nu=0.05, dt=0.1, bc=PER)
