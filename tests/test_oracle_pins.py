@@ -311,6 +311,37 @@ def test_predictor_conserves_momentum_periodic():
     assert np.all(np.abs(Hs) < 1e-11 * np.abs(H).sum())
 
 
+_UIN = np.array([0.8, -0.3, 0.2])
+_BC_FIELDS = {
+    # face tested, boundary conditions, a linear field satisfying that face's condition, normal axis
+    "inflow": ((1, 2, 0, 0, 0, 0), lambda x: _UIN[:, None] + np.outer([0.3, -0.2, 0.45], x[:, 0]), 0),
+    "noslip": ((0, 0, 0, 0, 4, 3), lambda x: np.outer([0.3, -0.2, 0.45], x[:, 2]), 2),
+    "slip": ((0, 0, 3, 3, 0, 0),
+             lambda x: np.stack([np.full(len(x), 0.7), 0.35 * x[:, 1], np.full(len(x), -0.4)]), 1),
+}
+
+
+@pytest.mark.parametrize("face", sorted(_BC_FIELDS))
+def test_boundary_ghosts_are_exact_for_linear_fields(face):
+    """The outer boundary ghosts (reading; the paper omits them) are linear extrapolations.  They are
+    2 u_in - u_P at the inflow, -u_P at a no-slip wall, and at a slip wall the normal component
+    mirrored and the tangential ones copied.  So the viscous operator of a linear field that meets the
+    face's condition (Dirichlet value u_in at the inflow face, zero at the no-slip face, zero normal
+    component and no normal variation of the tangential ones at a slip face) vanishes in the cells
+    next to that face.  A plain u_in ghost at the inflow, swapped slip parities or a copied no-slip
+    ghost each leave 0.01-0.07 there."""
+    bc, field, ax = _BC_FIELDS[face]
+    n = (10, 9, 8)
+    N = n[0] * n[1] * n[2]
+    xc = np.stack([np.arange(N) % n[0], (np.arange(N) // n[0]) % n[1], np.arange(N) // (n[0] * n[1])], 1) + 0.5
+    case = oracle.Case(*n, nu=0.05, dt=0.2, bc=bc, u_in=tuple(_UIN), csm_on=0)
+    u = field(xc).reshape(-1).copy()
+    L = case.momentum_operator(u, np.zeros(case.NF), np.zeros(N)).reshape(3, -1)
+    near = xc[:, ax] < n[ax] - 2        # away from the opposite face, whose condition the field breaks
+    assert np.abs(L[:, near]).max() < 1e-14
+    assert np.abs(L).max() > 1e-3       # the opposite face does see the field (the check is not empty)
+
+
 def test_viscous_and_sgs_stress_of_a_linear_field_vanish_at_a_wall():
     """Sec. 2.1 / Eq. SGSstress: for a linear velocity u = c + A x with constant nu and nu_t the stress
     divergence div(nu grad u + nu_t (grad u + grad u^T)) is zero.  With the face velocities set to zero
