@@ -11,9 +11,10 @@
  * face at x = i*dx), Uy[nx*(ny+1)*nz], Uz[nx*ny*(nz+1)].
  * Triangle soups are float32 [ntri][3 vertices][xyz] in grid units (dx = 1 in the soup).
  *
- * Parity unpinned: where the paper is silent the oracle states a reading, and two of them have no
- * independent check beyond invariants -- the dead-end threshold (or_forcing) and the zero-gradient
- * velocity ghost at the outflow face.  The placement of the forcing (or_forcing) is pinned by its
+ * Parity unpinned: where the paper is silent the oracle states a reading, and one of them has no
+ * independent check beyond invariants -- the zero-gradient velocity ghost at the outflow face.  The
+ * dead-end filter (or_forcing) is pinned to the printed threshold.  The placement of the forcing
+ * (or_forcing) is pinned by its
  * d = 0 limit and by the Taylor-Green convergence of Sec. 2.5; the transpose SGS term on cut faces
  * (or_predict, or_momentum_operator) by the vanishing stress divergence of a linear field at a wall
  * (any choice exact for linear fields would pass); the inflow, slip and no-slip velocity ghosts by

@@ -683,25 +683,27 @@ def test_forcing_imposes_the_wall_velocity_on_a_cell_the_wall_passes_through():
 
 
 def test_deadend_filter_cancels_forcing():
-    # a 1-cell slot: cell 4 in x is boxed by walls on -x,+x,-y,+y,-z (5 cut links)
+    """Eq. deadend_filter: the forcing is cancelled where at least 5 of the 6 axis links are blocked (at
+    most one open direction), and kept where two directions stay open.  Cell (4, 4, 4) of a 9^3 slip box
+    is walled in on 4, 5 or 6 sides by full planes."""
+    thr = GOLD["deadend_threshold"]["value"]
     n = 9
-    walls = []
     lo, hi = -40.0, 120.0     # right triangles whose legs span the whole cross-section
-    walls += [[[4.2, lo, lo], [4.2, hi, lo], [4.2, lo, hi]]]       # x = 4.2
-    walls += [[[4.8, lo, lo], [4.8, hi, lo], [4.8, lo, hi]]]       # x = 4.8
-    walls += [[[lo, 4.3, lo], [lo, 4.3, hi], [hi, 4.3, lo]]]       # y = 4.3
-    walls += [[[lo, 4.7, lo], [lo, 4.7, hi], [hi, 4.7, lo]]]       # y = 4.7
-    walls += [[[lo, lo, 4.2], [hi, lo, 4.2], [lo, hi, 4.2]]]       # z = 4.2
-    tri = np.array(walls, np.float32)
-    for on in (0, 1):
-        case = oracle.Case(n, n, n, bc=SLIPBOX, deadend_on=on)
-        case.set_geometry(tri)
-        P = 4 + n * (4 + n * 4)
-        assert bin(int(case.flags[P]) & 63).count("1") == 5
-        u = np.ones(3 * case.N)
-        o, _ = case.forcing(u)
-        changed = o[P] != 1.0
-        assert changed == (on == 0)
+    planes = {
+        "x-": [[4.2, lo, lo], [4.2, hi, lo], [4.2, lo, hi]], "x+": [[4.8, lo, lo], [4.8, hi, lo], [4.8, lo, hi]],
+        "y-": [[lo, 4.3, lo], [lo, 4.3, hi], [hi, 4.3, lo]], "y+": [[lo, 4.7, lo], [lo, 4.7, hi], [hi, 4.7, lo]],
+        "z-": [[lo, lo, 4.2], [hi, lo, 4.2], [lo, hi, 4.2]], "z+": [[lo, lo, 4.8], [hi, lo, 4.8], [lo, hi, 4.8]],
+    }
+    P = 4 + n * (4 + n * 4)
+    for walls in (["x-", "x+", "y-", "y+"], ["x-", "x+", "y-", "y+", "z-"], sorted(planes)):
+        tri = np.array([planes[w] for w in walls], np.float32)
+        for on in (0, 1):
+            case = oracle.Case(n, n, n, bc=SLIPBOX, deadend_on=on)
+            case.set_geometry(tri)
+            assert bin(int(case.flags[P]) & 63).count("1") == len(walls)
+            o, _ = case.forcing(np.ones(3 * case.N))
+            forced = o[P] != 1.0
+            assert forced == (on == 0 or len(walls) < thr), (walls, on)
 
 
 # --------------------------------------------------------------------------------------------------
