@@ -7,7 +7,7 @@ Boundary-type codes (one per domain face, order x-, x+, y-, y+, z-, z+):
   0 periodic, 1 inflow (Dirichlet u_in), 2 outflow (zero normal gradient, p = 0), 3 slip wall,
   4 no-slip wall.
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import Callable, Optional
 import numpy as np
 
