@@ -11,14 +11,16 @@
  * face at x = i*dx), Uy[nx*(ny+1)*nz], Uz[nx*ny*(nz+1)].
  * Triangle soups are float32 [ntri][3 vertices][xyz] in grid units (dx = 1 in the soup).
  *
- * Parity unpinned: where the paper is silent the oracle states a reading, and one of them has no
- * independent check beyond invariants -- the zero-gradient velocity ghost at the outflow face.  The
- * other readings are pinned: the dead-end filter (or_forcing) to the printed threshold; the
- * placement of the forcing (or_forcing) by its d = 0 limit and by the Taylor-Green convergence of
- * Sec. 2.5; the transpose SGS term on cut faces (or_predict, or_momentum_operator) by the vanishing
- * stress divergence of a linear field at a wall (any choice exact for linear fields would pass); the
- * inflow, slip and no-slip velocity ghosts by their exactness for linear fields; the pressure part
- * of the outer boundaries by a manufactured solution at second order.
+ * Readings and their pins: where the paper is silent the oracle states a reading, and each one has
+ * a check beyond the oracle's own definition.  The dead-end filter (or_forcing) is pinned to the
+ * printed threshold; the placement of the forcing (or_forcing) by its d = 0 limit and by the
+ * Taylor-Green convergence of Sec. 2.5; the transpose SGS term on cut faces (or_predict,
+ * or_momentum_operator) by the vanishing stress divergence of a linear field at a wall (any choice
+ * exact for linear fields would pass); the inflow, slip and no-slip velocity ghosts by their
+ * exactness for linear fields; the zero-gradient outflow velocity ghost by an x-invariant field,
+ * whose operator next to the outflow face equals the interior one (the inflow, slip and no-slip
+ * ghosts fail that check); the pressure part of the outer boundaries by a manufactured solution at
+ * second order.
  */
 #ifndef IBM_ORACLE_H
 #define IBM_ORACLE_H

@@ -342,6 +342,44 @@ def test_boundary_ghosts_are_exact_for_linear_fields(face):
     assert np.abs(L).max() > 1e-3       # the opposite face does see the field (the check is not empty)
 
 
+def _x_invariant_field(n):
+    """A velocity that does not vary along x: smooth periodic modes in y and z."""
+    N = n[0] * n[1] * n[2]
+    xc = np.stack([np.arange(N) % n[0], (np.arange(N) // n[0]) % n[1], np.arange(N) // (n[0] * n[1])], 1) + 0.5
+    ty, tz = 2 * np.pi * xc[:, 1] / n[1], 2 * np.pi * xc[:, 2] / n[2]
+    u = np.stack([0.7 + 0.2 * np.sin(ty) + 0.1 * np.cos(tz), -0.3 + 0.15 * np.cos(ty) * np.sin(tz),
+                  0.4 + 0.25 * np.sin(tz) - 0.1 * np.cos(2 * ty)])
+    return xc, u.reshape(-1).copy()
+
+
+@pytest.mark.parametrize("xplus,expect_exact", [(2, True), (1, False), (3, False), (4, False)])
+def test_outflow_ghost_is_a_zero_normal_gradient(xplus, expect_exact):
+    """Reading of the outflow face (the paper leaves the outer boundaries out, Sec. 2.1): the velocity
+    ghost across it is the near cell's own value, so the face imposes a zero normal gradient.  For a
+    field that does not vary along x, the momentum operator (diffusion plus the transpose SGS term
+    with a uniform nu_t; no advection) must then be the same in the cells next to the x+ face as in
+    interior cells with the same (y, z), because a zero-gradient face adds no flux.  The same field
+    with the x+ face read instead as an inflow (ghost 2 u_in - u_P), a slip wall (normal component
+    mirrored) or a no-slip wall (ghost -u_P) differs there by more than 1e-3, so the check tells the
+    outflow ghost apart from every other ghost the oracle has."""
+    n = (12, 10, 8)
+    xc, u = _x_invariant_field(n)
+    bc = (1, xplus, 0, 0, 0, 0)
+    case = oracle.Case(*n, nu=0.05, dt=0.2, bc=bc, u_in=(0.8, -0.3, 0.2), csm_on=0)
+    N = case.N
+    L = case.momentum_operator(u, np.zeros(case.NF), np.full(N, 0.07)).reshape(3, n[2], n[1], n[0])
+    edge, mid = L[:, :, :, n[0] - 1], L[:, :, :, n[0] // 2]
+    scale = np.abs(mid).max()
+    assert scale > 1e-3                        # the field has a nonzero operator (the check is not empty)
+    gap = np.abs(edge - mid).max()
+    if expect_exact:
+        assert gap <= 1e-14 * max(scale, 1.0)
+        # and the interior column is x-invariant as well (the inflow face is two cells away from it)
+        assert np.abs(L[:, :, :, 2:] - mid[..., None]).max() <= 1e-14 * max(scale, 1.0)
+    else:
+        assert gap > 1e-3
+
+
 def test_viscous_and_sgs_stress_of_a_linear_field_vanish_at_a_wall():
     """Sec. 2.1 / Eq. SGSstress: for a linear velocity u = c + A x with constant nu and nu_t the stress
     divergence div(nu grad u + nu_t (grad u + grad u^T)) is zero.  With the face velocities set to zero
