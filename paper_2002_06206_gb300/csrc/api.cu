@@ -132,14 +132,7 @@ static void free_state(les_state* S) {
         free(w);
     }
     if (S->c.mg) {
-        for (int l = 1; l < S->c.mg->nlev; ++l) {
-            MGLev& L = S->c.mg->lev[l];
-            for (int a = 0; a < 3; ++a) cudaFree(L.g[a]);
-            cudaFree(L.d);
-            cudaFree(L.invdg);
-            cudaFree(L.b);
-            cudaFree(L.x);
-        }
+        mg_free(*S->c.mg);
         free(S->c.mg);
     }
     prof_free(S->c.prof);
@@ -312,30 +305,12 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
         mg->sweeps = p->mg_sweeps > 0 ? p->mg_sweeps : 2;
         mg->omega = p->mg_omega > 0.0 ? p->mg_omega : 1.6;
         mg->coarse_sweeps = 8;
-        int dims[IBM_MG_MAXLEV][3];
-        mg->nlev = mg_levels_for(g->nx, g->ny, g->nz, dims, IBM_MG_MAXLEV);
-        for (int l = 0; l < mg->nlev; ++l) {
-            MGLev& L = mg->lev[l];
-            L.nx = dims[l][0];
-            L.ny = dims[l][1];
-            L.nz = dims[l][2];
-            L.sy = L.nx;
-            L.sz = (long long)L.nx * L.ny;
-            L.N = L.sz * L.nz;
-            for (int a = 0; a < 3; ++a) L.per[a] = p->bc[2 * a] == IBM_BC_PERIODIC;
-            if (l == 0) continue;
-            for (int a = 0; a < 3; ++a) ALLOC(L.g[a], (size_t)L.N * sizeof(float));
-            ALLOC(L.d, (size_t)L.N * sizeof(float));
-            ALLOC(L.invdg, (size_t)L.N * sizeof(float));
-            ALLOC(L.b, (size_t)L.N * s);
-            ALLOC(L.x, (size_t)L.N * s);
-        }
         ALLOC(S->w.z, N * s);
         if ((e = cudaStreamCreateWithFlags(&S->w.cap, cudaStreamNonBlocking)) != cudaSuccess) {
             free_state(S);
             return ibm_cuda_check(e, "les_create: capture stream");
         }
-        int rc2 = mg_setup(S->c, *mg, 0);
+        int rc2 = mg_setup(S->c, *mg, (int)s);
         if (!rc2 && (e = cudaDeviceSynchronize()) != cudaSuccess) rc2 = ibm_cuda_check(e, "les_create: multigrid set-up");
         if (rc2) {
             free_state(S);

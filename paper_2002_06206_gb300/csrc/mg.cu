@@ -4,17 +4,25 @@
 //
 // Level 0 is the fine grid: the conductance of a link is 1 when its face is uncut and inside the
 // domain (or across a periodic seam), 0 otherwise, and an outflow face adds 2 to the diagonal (ghost
-// -p).  A coarse cell aggregates the 2x2x2 fine cells below it; with piecewise-constant prolongation
-// P and restriction R = P^T the Galerkin coarse operator R A P is again a 7-point operator whose link
-// conductance is the sum of the fine conductances crossing the coarse face, so walls seen by the fine
-// grid weaken the coarse links in proportion.  The V-cycle (pre-smoothing red then black,
-// post-smoothing black then red, the coarse correction scaled by omega < 2, symmetric sweeps on the
-// coarsest grid) is a symmetric operator, as CG requires.
+// -p).  A position of level l >= 1 is a block of 2x2x2 positions of level l - 1, and its unknowns are
+// the connected parts of that block: unknowns of level l - 1 inside the block joined by their links
+// inside the block.  So an aggregate never spans a wall -- a block cut in two by a thin plate gives
+// two coarse unknowns, and a sealed pocket (the inside of a closed part of the soup) never merges
+// with its surroundings on any level.  (Aggregating whole blocks instead joins the two sides of every
+// wall on the coarse levels; on a dirty multi-part soup that costs several times the iterations.)
+// With piecewise-constant prolongation P and restriction R = P^T the Galerkin coarse operator R A P
+// is again a weighted graph Laplacian plus the outflow terms: the conductance between two coarse
+// unknowns is the sum of the fine conductances between their aggregates.  Links join only
+// face-neighbouring positions, so the parity of a position two-colours every level.  The V-cycle
+// (pre-smoothing red then black, post-smoothing black then red, the coarse correction scaled by
+// omega < 2, symmetric sweeps on the coarsest level) is a symmetric operator, as CG requires.
 //
 // Equations are solved in the unscaled form  sum_links g (x_N - x_P) - d x_P = dx^2 r.
 #include <cooperative_groups.h>
+#include <string.h>
 #include <type_traits>
 
+#include "scan.cuh"
 #include "solver.cuh"
 
 namespace cg = cooperative_groups;
@@ -22,7 +30,12 @@ namespace cg = cooperative_groups;
 namespace {
 
 #define MG_TAIL_CTAS 8          // portable cluster size
-#define MG_TAIL_MAX_CELLS (1LL << 13)
+#define MG_TAIL_MAX (1LL << 13) // levels with at most this many unknowns run in the one-launch tail
+#define MG_COARSE_TARGET 1024   // coarsening stops at this many unknowns (or one position)
+#define MG_MAXCH 64             // unknowns of a block whose internal links are followed (more: singletons)
+#define MG_MAXE 256             // internal links followed per block
+#define MG_MAXL 64              // distinct neighbours of a coarse unknown (more: the level is dropped)
+#define MG_L1L 24               // level 1: a 2x2x2 block has at most 24 links leaving it
 
 struct MGTail {
     MGLev lev[IBM_MG_MAXLEV];
@@ -31,6 +44,7 @@ struct MGTail {
 };
 
 __device__ __forceinline__ unsigned flags_at(const Dom& D, long long P) { return D.flags ? (unsigned)D.flags[P] : 0u; }
+
 
 // Conductances and Dirichlet term of a fine (level 0) cell, links in the order x-, x+, y-, y+, z-, z+.
 __device__ __forceinline__ void fine_links(const Dom& D, long long P, const int x[3], unsigned fl, float g[6],
@@ -47,30 +61,6 @@ __device__ __forceinline__ void fine_links(const Dom& D, long long P, const int 
     }
 }
 
-// Neighbour offset on a coarse level (periodic axes wrap).
-__device__ __forceinline__ bool lev_off(const MGLev& L, int a, int s, int xa, long long& off) {
-    const int n = a == 0 ? L.nx : (a == 1 ? L.ny : L.nz);
-    const long long st = a == 0 ? 1 : (a == 1 ? L.sy : L.sz);
-    const int y = xa + s;
-    if (y >= 0 && y < n) { off = s * st; return true; }
-    if (!L.per[a]) return false;
-    off = -(long long)s * (n - 1) * st;
-    return true;
-}
-
-// Coarse cell links: g of the -a link is the +a link of the lower neighbour.
-__device__ __forceinline__ void coarse_links(const MGLev& L, long long P, const int x[3], float g[6], long long off[6]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        long long om = 0, op = 0;
-        const bool inm = lev_off(L, a, -1, x[a], om);
-        const bool inp = lev_off(L, a, +1, x[a], op);
-        off[2 * a] = om;
-        off[2 * a + 1] = op;
-        g[2 * a] = inm ? L.g[a][P + om] : 0.f;
-        g[2 * a + 1] = inp ? L.g[a][P] : 0.f;
-    }
-}
 
 // Cell coordinates from a linear index (grids hold fewer than 2^31 cells: 32-bit division).
 __device__ __forceinline__ void coords3(long long c, int nx, int ny, int x[3]) {
@@ -82,74 +72,12 @@ __device__ __forceinline__ void coords3(long long c, int nx, int ny, int x[3]) {
     x[2] = (int)z;
 }
 
-// ---- set-up -------------------------------------------------------------------------------------
 
-// Level 1 from the fine grid: conductances of the coarse +a links and the Dirichlet term.
-__global__ void k_mg_build1(Dom D, MGLev C) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.N; q += (long long)gridDim.x * blockDim.x) {
-        int X[3];
-        coords3(q, C.nx, C.ny, X);
-        const int n[3] = {D.nx, D.ny, D.nz};
-        float ga[3] = {0.f, 0.f, 0.f}, dsum = 0.f;
-        for (int dk = 0; dk < 2; ++dk)
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    const int x[3] = {2 * X[0] + di, 2 * X[1] + dj, 2 * X[2] + dk};
-                    if (x[0] >= n[0] || x[1] >= n[1] || x[2] >= n[2]) continue;
-                    const long long P = x[0] + (long long)D.sy * x[1] + D.sz * x[2];
-                    float g[6], d;
-                    long long off[6];
-                    fine_links(D, P, x, flags_at(D, P), g, off, d);
-                    dsum += d;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        if ((x[a] & 1) || x[a] + 1 == n[a]) ga[a] += g[2 * a + 1];   // crosses the coarse +a face
-                }
-        C.g[0][q] = ga[0];
-        C.g[1][q] = ga[1];
-        C.g[2][q] = ga[2];
-        C.d[q] = dsum;
-    }
+__device__ __forceinline__ long long pos_index(const MGLev& L, const int X[3]) {
+    return X[0] + (long long)L.px * (X[1] + (long long)L.py * X[2]);
 }
 
-// Level l + 1 from level l.
-__global__ void k_mg_build_next(MGLev F, MGLev C) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.N; q += (long long)gridDim.x * blockDim.x) {
-        int X[3];
-        coords3(q, C.nx, C.ny, X);
-        const int n[3] = {F.nx, F.ny, F.nz};
-        float ga[3] = {0.f, 0.f, 0.f}, dsum = 0.f;
-        for (int dk = 0; dk < 2; ++dk)
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    const int x[3] = {2 * X[0] + di, 2 * X[1] + dj, 2 * X[2] + dk};
-                    if (x[0] >= n[0] || x[1] >= n[1] || x[2] >= n[2]) continue;
-                    const long long P = x[0] + F.sy * x[1] + F.sz * x[2];
-                    dsum += F.d[P];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        if ((x[a] & 1) || x[a] + 1 == n[a]) ga[a] += F.g[a][P];
-                }
-        C.g[0][q] = ga[0];
-        C.g[1][q] = ga[1];
-        C.g[2][q] = ga[2];
-        C.d[q] = dsum;
-    }
-}
-
-__global__ void k_mg_invdiag(MGLev L) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L.N; q += (long long)gridDim.x * blockDim.x) {
-        int x[3];
-        coords3(q, L.nx, L.ny, x);
-        float g[6];
-        long long off[6];
-        coarse_links(L, q, x, g, off);
-        const float dg = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + L.d[q];
-        L.invdg[q] = dg > 0.f ? 1.f / dg : 0.f;
-    }
-}
-
-// ---- smoothing, transfer ------------------------------------------------------------------------
+// ---- fine-grid smoothing ----------------------------------------------------------------------
 
 // Gauss-Seidel value of a fine cell:  z_P = (sum_links g z_N - scale r_P) / dg, with the interior
 // fast path (six uncut links, dg = 6).  Returns false for an isolated cell (dg = 0).
@@ -201,221 +129,6 @@ __global__ void __launch_bounds__(256) k_mg_smooth0(Dom D, const T* __restrict__
     }
 }
 
-// One red-black pass of colour `col` on a coarse level.  Work item t covers the t-th cell of that
-// colour (row-major over the half-rows), t = t0, t0 + nt, ...; with `zero` the iterate is taken as 0
-// and the cell of the other colour next to it is cleared.
-template <class T>
-__device__ __forceinline__ void smooth_level(const MGLev& L, int col, bool zero, long long t0, long long nt) {
-    const T* __restrict__ b = (const T*)L.b;
-    T* __restrict__ x = (T*)L.x;
-    const int hx = (L.nx + 1) >> 1;
-    const long long n = (long long)hx * L.ny * L.nz;
-    for (long long t = t0; t < n; t += nt) {
-        int c[3];
-        coords3(t, hx, L.ny, c);
-        const int par = (col + c[1] + c[2]) & 1;
-        const int x0 = 2 * c[0] + par, x1 = 2 * c[0] + (par ^ 1);
-        const long long row = L.sy * c[1] + L.sz * c[2];
-        if (zero && x1 < L.nx) x[row + x1] = (T)0;
-        if (x0 >= L.nx) continue;
-        c[0] = x0;
-        const long long q = row + x0;
-        const float inv = L.invdg[q];
-        if (inv == 0.f) { x[q] = (T)0; continue; }
-        T s = 0;
-        if (!zero) {
-            float g[6];
-            long long off[6];
-            coarse_links(L, q, c, g, off);
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-                if (g[e] != 0.f) s += (T)g[e] * x[q + off[e]];
-        }
-        x[q] = (s - b[q]) * (T)inv;
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_mg_smoothc(MGLev L, int col, int zero, const SolveScal* sc) {
-    if (sc->done) return;
-    smooth_level<T>(L, col, zero != 0, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                    (long long)gridDim.x * blockDim.x);
-}
-
-// Residual of level 0 restricted to level 1: each coarse cell sums the residuals of its children.
-template <class T>
-__global__ void k_mg_restrict0(Dom D, const T* __restrict__ r, const T* __restrict__ z, T scale, MGLev C,
-                               const SolveScal* sc) {
-    if (sc->done) return;
-    T* __restrict__ bc = (T*)C.b;
-    const int n[3] = {D.nx, D.ny, D.nz};
-    auto zv = [&](long long c) { return z[c]; };
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.N; q += (long long)gridDim.x * blockDim.x) {
-        int X[3];
-        coords3(q, C.nx, C.ny, X);
-        T acc = 0;
-#pragma unroll
-        for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-            for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-                for (int di = 0; di < 2; ++di) {
-                    const int x0 = 2 * X[0] + di, x1 = 2 * X[1] + dj, x2 = 2 * X[2] + dk;
-                    if (x0 >= n[0] || x1 >= n[1] || x2 >= n[2]) continue;
-                    const long long P = x0 + (long long)D.sy * x1 + D.sz * x2;
-                    const T az = link_sum7<T>(D, P, x0, x1, x2, flags_at(D, P), z[P], zv);
-                    acc += scale * r[P] - az;
-                }
-        bc[q] = acc;
-    }
-}
-
-// Residual of coarse level F restricted to level C (sum over the children).
-template <class T>
-__device__ __forceinline__ void restrict_level(const MGLev& F, const MGLev& C, long long t0, long long nt) {
-    const T* __restrict__ bf = (const T*)F.b;
-    const T* __restrict__ xf = (const T*)F.x;
-    T* __restrict__ bc = (T*)C.b;
-    const int n[3] = {F.nx, F.ny, F.nz};
-    for (long long q = t0; q < C.N; q += nt) {
-        int X[3];
-        coords3(q, C.nx, C.ny, X);
-        T acc = 0;
-        for (int dk = 0; dk < 2; ++dk)
-            for (int dj = 0; dj < 2; ++dj)
-                for (int di = 0; di < 2; ++di) {
-                    const int x[3] = {2 * X[0] + di, 2 * X[1] + dj, 2 * X[2] + dk};
-                    if (x[0] >= n[0] || x[1] >= n[1] || x[2] >= n[2]) continue;
-                    const long long P = x[0] + F.sy * x[1] + F.sz * x[2];
-                    float g[6];
-                    long long off[6];
-                    coarse_links(F, P, x, g, off);
-                    const T xP = xf[P];
-                    T ax = -(T)F.d[P] * xP;
-#pragma unroll
-                    for (int e = 0; e < 6; ++e)
-                        if (g[e] != 0.f) ax += (T)g[e] * (xf[P + off[e]] - xP);
-                    acc += bf[P] - ax;
-                }
-        bc[q] = acc;
-    }
-}
-
-template <class T>
-__global__ void k_mg_restrictc(MGLev F, MGLev C, const SolveScal* sc) {
-    if (sc->done) return;
-    restrict_level<T>(F, C, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
-}
-
-// Coarse correction: x_fine += omega * x_coarse(parent), level 0 or a coarse level.
-template <class T>
-__device__ __forceinline__ void prolong_level(long long N, int nx, int ny, T* __restrict__ xf, const MGLev& C, T omega,
-                                              long long t0, long long nt) {
-    const T* __restrict__ xc = (const T*)C.x;
-    for (long long q = t0; q < N; q += nt) {
-        int x[3];
-        coords3(q, nx, ny, x);
-        const long long parent = (x[0] >> 1) + C.sy * (x[1] >> 1) + C.sz * (x[2] >> 1);
-        xf[q] = xf[q] + omega * xc[parent];
-    }
-}
-
-template <class T>
-__global__ void k_mg_prolong(long long N, int nx, int ny, T* __restrict__ xf, const MGLev C, T omega,
-                             const SolveScal* sc) {
-    if (sc->done) return;
-    prolong_level<T>(N, nx, ny, xf, C, omega, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                     (long long)gridDim.x * blockDim.x);
-}
-
-// Coarsest level (at most 1024 cells, one block of 1024 threads, one cell per thread): `sweeps`
-// red-black passes then as many black-red (a symmetric operator).  Each thread keeps its links and
-// right-hand side in registers; the iterate lives in shared memory.
-template <class T>
-__device__ __forceinline__ void coarsest_solve(const MGLev& L, int sweeps, T* xs) {
-    const long long q = threadIdx.x;
-    const bool act = q < L.N;
-    int col = 0;
-    float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, inv = 0.f;
-    int nb[6] = {0, 0, 0, 0, 0, 0};
-    T bq = 0;
-    if (act) {
-        int c[3];
-        coords3(q, L.nx, L.ny, c);
-        col = (c[0] + c[1] + c[2]) & 1;
-        long long off[6];
-        coarse_links(L, q, c, g, off);
-#pragma unroll
-        for (int e = 0; e < 6; ++e) nb[e] = (int)(q + off[e]);
-        inv = L.invdg[q];
-        bq = ((const T*)L.b)[q];
-    }
-    xs[threadIdx.x] = (T)0;
-    __syncthreads();
-    for (int pass = 0; pass < 4 * sweeps; ++pass) {
-        const int half = pass / (2 * sweeps);                 // 0: red-black order, 1: black-red
-        const int want = ((pass & 1) ^ half);
-        if (act && col == want && inv != 0.f) {
-            T s = 0;
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-                if (g[e] != 0.f) s += (T)g[e] * xs[nb[e]];
-            xs[threadIdx.x] = (s - bq) * (T)inv;
-        }
-        __syncthreads();
-    }
-    if (act) ((T*)L.x)[q] = xs[threadIdx.x];
-}
-
-template <class T>
-__global__ void __launch_bounds__(1024) k_mg_coarsest(MGLev L, int sweeps, const SolveScal* sc) {
-    if (sc->done) return;
-    __shared__ T xs[1024];
-    coarsest_solve<T>(L, sweeps, xs);
-}
-
-// The small levels first .. nlev-1 of a V-cycle in one launch: one cluster of MG_TAIL_CTAS blocks of
-// 1024 threads walks the descent (smoothing, restriction), the coarsest solve (block 0) and the
-// ascent (prolongation, smoothing), with a cluster barrier (hardware, release/acquire at cluster
-// scope) between dependent passes.  These levels are a few MB at most and stay in L2; as separate
-// kernels each pass would cost a launch for a few microseconds of work.
-template <class T>
-__global__ void __launch_bounds__(1024) k_mg_tail(MGTail M, const SolveScal* sc) {
-    if (sc->done) return;                       // the flag is uniform: set by an earlier kernel
-    __shared__ T xs[1024];
-    cg::cluster_group cl = cg::this_cluster();
-    const long long t0 = (long long)cl.block_rank() * blockDim.x + threadIdx.x;
-    const long long nt = (long long)cl.num_blocks() * blockDim.x;
-    auto bar = [&]() {
-        __threadfence();
-        cl.sync();
-    };
-    const int last = M.nlev - 1;
-    for (int l = M.first; l < last; ++l) {
-        for (int q = 0; q < M.sweeps; ++q) {
-            smooth_level<T>(M.lev[l], 0, q == 0, t0, nt);
-            bar();
-            smooth_level<T>(M.lev[l], 1, false, t0, nt);
-            bar();
-        }
-        restrict_level<T>(M.lev[l], M.lev[l + 1], t0, nt);
-        bar();
-    }
-    if (cl.block_rank() == 0) coarsest_solve<T>(M.lev[last], M.coarse_sweeps, xs);
-    bar();
-    for (int l = last - 1; l >= M.first; --l) {
-        const MGLev& F = M.lev[l];
-        prolong_level<T>(F.N, F.nx, F.ny, (T*)F.x, M.lev[l + 1], (T)M.omega, t0, nt);
-        bar();
-        for (int q = 0; q < M.sweeps; ++q) {
-            smooth_level<T>(F, 1, false, t0, nt);
-            bar();
-            smooth_level<T>(F, 0, false, t0, nt);
-            bar();
-        }
-    }
-}
-
 // Last pass of the V-cycle on level 0 (colour 0) fused with rho = (r, z) over both colours.
 template <class T>
 __global__ void __launch_bounds__(256) k_mg_final0(Dom D, const T* __restrict__ r, T* __restrict__ z, T scale,
@@ -449,6 +162,681 @@ __global__ void __launch_bounds__(256) k_mg_final0(Dom D, const T* __restrict__ 
     });
 }
 
+// ---- parts of a block -----------------------------------------------------------------------------
+
+// Flags of the 2x2x2 fine cells below level-1 position X (cell m = di + 2 dj + 4 dk); bit m of the
+// result says that cell m lies inside the domain.  Out-of-domain cells get flags 0.
+__device__ __forceinline__ unsigned block_flags(const Dom& D, const int X[3], unsigned (&fl)[8], long long (&P)[8]) {
+    unsigned in = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int x = 2 * X[0] + (m & 1), y = 2 * X[1] + ((m >> 1) & 1), z = 2 * X[2] + (m >> 2);
+        const bool ok = x < D.nx && y < D.ny && z < D.nz;
+        P[m] = ok ? x + (long long)D.sy * y + D.sz * z : 0;
+        fl[m] = ok ? flags_at(D, P[m]) : 0u;
+        in |= (ok ? 1u : 0u) << m;
+    }
+    return in;
+}
+
+// Connected parts of a fine block: two in-domain cells of the block are joined when the face between
+// them is uncut, or when their axis is periodic with only two cells (the seam joins them too).
+// part[m] = the part of cell m, parts numbered in the order of their lowest cell; returns the count.
+__device__ __forceinline__ int fine_parts(const Dom& D, const unsigned (&fl)[8], unsigned in, int (&part)[8]) {
+    const unsigned cut = ((fl[0] | fl[2] | fl[4] | fl[6]) & 2u) | ((fl[0] | fl[1] | fl[4] | fl[5]) & 8u) |
+                         ((fl[0] | fl[1] | fl[2] | fl[3]) & 32u);
+    if (in == 0xffu && cut == 0u) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) part[m] = 0;
+        return 1;
+    }
+    const bool seam[3] = {D.bc[0] == IBM_BC_PERIODIC && D.nx == 2, D.bc[2] == IBM_BC_PERIODIC && D.ny == 2,
+                          D.bc[4] == IBM_BC_PERIODIC && D.nz == 2};
+    int lab[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) lab[m] = m;
+    // minimum-label propagation; a path through the block has at most 7 links
+    for (int it = 0; it < 8; ++it) {
+        bool changed = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                if (m & (1 << a)) continue;
+                const int h = m | (1 << a);
+                if (!((in >> m) & 1u) || !((in >> h) & 1u)) continue;
+                if ((fl[m] & (2u << (2 * a))) && !seam[a]) continue;
+                const int lo = lab[m] < lab[h] ? lab[m] : lab[h];
+                if (lab[m] != lo || lab[h] != lo) {
+                    lab[m] = lo;
+                    lab[h] = lo;
+                    changed = true;
+                }
+            }
+        if (!changed) break;
+    }
+    unsigned roots = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        if (((in >> m) & 1u) && lab[m] == m) roots |= 1u << m;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) part[m] = __popc(roots & ((1u << lab[m]) - 1u));
+    return __popc(roots);
+}
+
+// ---- set-up -------------------------------------------------------------------------------------
+
+// Level 1: parts of every block (cnt) and the part of every fine cell (sub0).
+__global__ void k_parts1(Dom D, MGLev L, uint8_t* __restrict__ sub0) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L.P; q += (long long)gridDim.x * blockDim.x) {
+        int X[3];
+        coords3(q, L.px, L.py, X);
+        unsigned fl[8];
+        long long P[8];
+        const unsigned in = block_flags(D, X, fl, P);
+        int part[8];
+        L.cnt[q] = fine_parts(D, fl, in, part);
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if ((in >> m) & 1u) sub0[P[m]] = (uint8_t)part[m];
+    }
+}
+
+// Adds conductance g towards unknown v to a small table of distinct neighbours; false when full.
+template <int CAP>
+__device__ __forceinline__ bool table_add(int (&nb)[CAP], float (&gv)[CAP], int& n, int v, float g) {
+    for (int e = 0; e < n; ++e)
+        if (nb[e] == v) {
+            gv[e] += g;
+            return true;
+        }
+    if (n == CAP) return false;
+    nb[n] = v;
+    gv[n] = g;
+    ++n;
+    return true;
+}
+
+// Writes a row sorted by neighbour index (insertion sort; rows are short).
+template <int CAP>
+__device__ __forceinline__ float write_row(const MGLev& L, long long u, int (&nb)[CAP], float (&gv)[CAP], int n) {
+    for (int e = 1; e < n; ++e) {
+        const int v = nb[e];
+        const float w = gv[e];
+        int f = e - 1;
+        while (f >= 0 && nb[f] > v) {
+            nb[f + 1] = nb[f];
+            gv[f + 1] = gv[f];
+            --f;
+        }
+        nb[f + 1] = v;
+        gv[f + 1] = w;
+    }
+    const long long k0 = L.rp[u];
+    float gs = 0.f;
+    for (int e = 0; e < n; ++e) {
+        L.col[k0 + e] = nb[e];
+        L.g[k0 + e] = gv[e];
+        gs += gv[e];
+    }
+    return gs;
+}
+
+// Level 1 links.  Count pass (fill = 0): rp[u] = distinct neighbours, d, pos.  Fill pass: the sorted
+// row, invdg.  A fine link leaving the block joins the part of its cell to the part of the cell across.
+__global__ void k_links1(Dom D, MGLev L, const uint8_t* __restrict__ sub0, int fill, int* ovf) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < L.P; q += (long long)gridDim.x * blockDim.x) {
+        int X[3];
+        coords3(q, L.px, L.py, X);
+        unsigned fl[8];
+        long long P[8];
+        const unsigned in = block_flags(D, X, fl, P);
+        const int np = L.cnt[q];
+        const int n3[3] = {D.nx, D.ny, D.nz};
+        for (int s = 0; s < np; ++s) {
+            const long long u = L.off[q] + s;
+            int nb[MG_L1L];
+            float gv[MG_L1L];
+            int n = 0;
+            float dsum = 0.f;
+            for (int m = 0; m < 8; ++m) {
+                if (!((in >> m) & 1u) || sub0[P[m]] != s) continue;
+                const int x[3] = {2 * X[0] + (m & 1), 2 * X[1] + ((m >> 1) & 1), 2 * X[2] + (m >> 2)};
+                for (int b = 0; b < 6; ++b) {
+                    if (fl[m] & (1u << b)) continue;
+                    const int a = b >> 1, sd = (b & 1) ? 1 : -1;
+                    long long o;
+                    if (!nb_offset(D, a, sd, x[a], o)) {
+                        if (D.bc[b] == IBM_BC_OUTFLOW) dsum += 2.f;
+                        continue;
+                    }
+                    int y[3] = {x[0], x[1], x[2]};
+                    y[a] += sd;
+                    if (y[a] < 0) y[a] = n3[a] - 1;
+                    if (y[a] >= n3[a]) y[a] = 0;
+                    const int Y[3] = {y[0] >> 1, y[1] >> 1, y[2] >> 1};
+                    if (Y[0] == X[0] && Y[1] == X[1] && Y[2] == X[2]) continue;      // inside the block
+                    const int v = L.off[pos_index(L, Y)] + sub0[P[m] + o];
+                    if (!table_add<MG_L1L>(nb, gv, n, v, 1.f)) *ovf = 1;
+                }
+            }
+            if (!fill) {
+                L.rp[u] = n;
+                L.d[u] = dsum;
+                L.pos[u] = (int32_t)q;
+            } else {
+                const float gs = write_row<MG_L1L>(L, u, nb, gv, n);
+                L.invdg[u] = gs + dsum > 0.f ? 1.f / (gs + dsum) : 0.f;
+            }
+        }
+    }
+}
+
+// Children of coarse position Y: the unknowns of the (up to) 8 positions of level F below it, in
+// position order.  Returns how many there are; the first MG_MAXCH go into list.
+__device__ __forceinline__ int block_children(const MGLev& F, const int Y[3], int (&list)[MG_MAXCH]) {
+    int n = 0;
+    for (int m = 0; m < 8; ++m) {
+        const int X[3] = {2 * Y[0] + (m & 1), 2 * Y[1] + ((m >> 1) & 1), 2 * Y[2] + (m >> 2)};
+        if (X[0] >= F.px || X[1] >= F.py || X[2] >= F.pz) continue;
+        const long long q = pos_index(F, X);
+        const int o = F.off[q], c = F.cnt[q];
+        for (int k = 0; k < c; ++k, ++n)
+            if (n < MG_MAXCH) list[n] = o + k;
+    }
+    return n;
+}
+
+// Level l + 1 from level l (= F): parts of each block of 8 positions.  F.parent[u] receives the part
+// of u within its block (made global by k_parent_next).  Children beyond MG_MAXCH, and internal links
+// beyond MG_MAXE, are not followed: such children stay parts of their own (a finer partition is as
+// valid an aggregation).
+__global__ void k_parts_next(MGLev F, MGLev C) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.P; q += (long long)gridDim.x * blockDim.x) {
+        int Y[3];
+        coords3(q, C.px, C.py, Y);
+        int list[MG_MAXCH];
+        const int ntot = block_children(F, Y, list);
+        const int n = ntot < MG_MAXCH ? ntot : MG_MAXCH;
+        uint8_t ea[MG_MAXE], eb[MG_MAXE];
+        int ne = 0;
+        for (int k = 0; k < n; ++k) {
+            const int u = list[k];
+            for (int e = F.rp[u]; e < F.rp[u + 1]; ++e) {
+                const int w = F.col[e];
+                if (w < u) continue;                       // each internal link once
+                int Xw[3];
+                coords3(F.pos[w], F.px, F.py, Xw);
+                if ((Xw[0] >> 1) != Y[0] || (Xw[1] >> 1) != Y[1] || (Xw[2] >> 1) != Y[2]) continue;
+                int kw = -1;
+                for (int t = 0; t < n; ++t)
+                    if (list[t] == w) {
+                        kw = t;
+                        break;
+                    }
+                if (kw < 0 || ne == MG_MAXE) continue;
+                ea[ne] = (uint8_t)k;
+                eb[ne] = (uint8_t)kw;
+                ++ne;
+            }
+        }
+        uint8_t lab[MG_MAXCH];
+        for (int k = 0; k < n; ++k) lab[k] = (uint8_t)k;
+        for (int it = 0; it < n; ++it) {
+            bool changed = false;
+            for (int e = 0; e < ne; ++e) {
+                const uint8_t lo = lab[ea[e]] < lab[eb[e]] ? lab[ea[e]] : lab[eb[e]];
+                if (lab[ea[e]] != lo || lab[eb[e]] != lo) {
+                    lab[ea[e]] = lo;
+                    lab[eb[e]] = lo;
+                    changed = true;
+                }
+            }
+            if (!changed) break;
+        }
+        // part numbers: roots in list order, then the children that were not followed
+        int nroot = 0;
+        uint8_t rank[MG_MAXCH];
+        for (int k = 0; k < n; ++k)
+            if (lab[k] == k) rank[k] = (uint8_t)nroot++;
+        for (int k = 0; k < n; ++k) F.parent[list[k]] = rank[lab[k]];
+        if (ntot > n) {
+            int extra = 0;
+            for (int m = 0; m < 8; ++m) {
+                const int X[3] = {2 * Y[0] + (m & 1), 2 * Y[1] + ((m >> 1) & 1), 2 * Y[2] + (m >> 2)};
+                if (X[0] >= F.px || X[1] >= F.py || X[2] >= F.pz) continue;
+                const long long qx = pos_index(F, X);
+                for (int k = 0; k < F.cnt[qx]; ++k, ++extra)
+                    if (extra >= MG_MAXCH) F.parent[F.off[qx] + k] = nroot + (extra - MG_MAXCH);
+            }
+        }
+        C.cnt[q] = nroot + (ntot - n);
+    }
+}
+
+__global__ void k_parent_next(MGLev F, MGLev C) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < F.M; u += (long long)gridDim.x * blockDim.x) {
+        int X[3];
+        coords3(F.pos[u], F.px, F.py, X);
+        const int Y[3] = {X[0] >> 1, X[1] >> 1, X[2] >> 1};
+        F.parent[u] = C.off[pos_index(C, Y)] + F.parent[u];
+    }
+}
+
+// Level l + 1 links (Galerkin sums) and children lists.  Count pass: rp[v] = distinct neighbours,
+// cp[v] = children, d, pos.  Fill pass: sorted rows, invdg, children.
+__global__ void k_links_next(MGLev F, MGLev C, int fill, int* ovf) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.P; q += (long long)gridDim.x * blockDim.x) {
+        int Y[3];
+        coords3(q, C.px, C.py, Y);
+        const int np = C.cnt[q];
+        for (int s = 0; s < np; ++s) {
+            const int v = C.off[q] + s;
+            int nb[MG_MAXL];
+            float gv[MG_MAXL];
+            int n = 0, nch = 0;
+            float dsum = 0.f;
+            for (int m = 0; m < 8; ++m) {
+                const int X[3] = {2 * Y[0] + (m & 1), 2 * Y[1] + ((m >> 1) & 1), 2 * Y[2] + (m >> 2)};
+                if (X[0] >= F.px || X[1] >= F.py || X[2] >= F.pz) continue;
+                const long long qx = pos_index(F, X);
+                for (int u = F.off[qx]; u < F.off[qx] + F.cnt[qx]; ++u) {
+                    if (F.parent[u] != v) continue;
+                    if (fill) C.ch[C.cp[v] + nch] = u;
+                    ++nch;
+                    dsum += F.d[u];
+                    for (int e = F.rp[u]; e < F.rp[u + 1]; ++e) {
+                        const int pw = F.parent[F.col[e]];
+                        if (pw == v) continue;
+                        if (!table_add<MG_MAXL>(nb, gv, n, pw, F.g[e])) *ovf = 1;
+                    }
+                }
+            }
+            if (!fill) {
+                C.rp[v] = n;
+                C.cp[v] = nch;
+                C.d[v] = dsum;
+                C.pos[v] = (int32_t)q;
+            } else {
+                const float gs = write_row<MG_MAXL>(C, v, nb, gv, n);
+                C.invdg[v] = gs + dsum > 0.f ? 1.f / (gs + dsum) : 0.f;
+            }
+        }
+    }
+}
+
+// Colour-major numbering of the unknowns: positions of colour c contribute cnt[q] unknowns each, in
+// position order, after all unknowns of colour 0 when c = 1.
+struct PosCount {
+    const int32_t* cnt;
+    int px, py, colour;
+    __device__ long long operator()(long long i) const {
+        int x[3];
+        coords3(i, px, py, x);
+        return ((x[0] + x[1] + x[2]) & 1) == colour ? cnt[i] : 0;
+    }
+};
+struct PosEmit {
+    int32_t* off;
+    int px, py, colour;
+    const long long* base;
+    __device__ void operator()(long long i, long long o, long long) const {
+        int x[3];
+        coords3(i, px, py, x);
+        if (((x[0] + x[1] + x[2]) & 1) == colour) off[i] = (int32_t)(o + (base ? *base : 0));
+    }
+};
+// In-place exclusive scan of a count array (rows, children).
+struct ArrCount {
+    const int32_t* a;
+    __device__ long long operator()(long long i) const { return a[i]; }
+};
+struct ArrEmit {
+    int32_t* a;
+    __device__ void operator()(long long i, long long o, long long) const { a[i] = (int32_t)o; }
+};
+
+// ---- the V-cycle on the coarse levels -----------------------------------------------------------
+
+// One red-black pass of colour `col` over the unknowns t0, t0 + nt, ... of that colour.  With `zero`
+// the iterate is taken as 0: colour `col` gets -b / dg and the other colour is cleared.
+template <class T>
+__device__ __forceinline__ void gsmooth(const MGLev& L, int col, bool zero, long long t0, long long nt) {
+    const T* __restrict__ b = (const T*)L.b;
+    T* x = (T*)L.x;
+    if (zero) {
+        for (long long u = t0; u < L.M; u += nt) {
+            const bool mine = (u < L.M0) == (col == 0);
+            x[u] = mine ? -b[u] * (T)L.invdg[u] : (T)0;
+        }
+        return;
+    }
+    const long long lo = col ? L.M0 : 0, hi = col ? L.M : L.M0;
+    for (long long u = lo + t0; u < hi; u += nt) {
+        T s = 0;
+        for (int e = L.rp[u]; e < L.rp[u + 1]; ++e) s += (T)L.g[e] * x[L.col[e]];
+        x[u] = (s - b[u]) * (T)L.invdg[u];
+    }
+}
+
+// b_C[v] = sum over the children u of v of the level-F residual  b_u - (sum g (x_w - x_u) - d_u x_u).
+template <class T>
+__device__ __forceinline__ void grestrict(const MGLev& F, const MGLev& C, long long t0, long long nt) {
+    const T* __restrict__ bf = (const T*)F.b;
+    const T* __restrict__ xf = (const T*)F.x;
+    T* __restrict__ bc = (T*)C.b;
+    for (long long v = t0; v < C.M; v += nt) {
+        T acc = 0;
+        for (int k = C.cp[v]; k < C.cp[v + 1]; ++k) {
+            const int u = C.ch[k];
+            const T xu = xf[u];
+            T ax = -(T)F.d[u] * xu;
+            for (int e = F.rp[u]; e < F.rp[u + 1]; ++e) ax += (T)F.g[e] * (xf[F.col[e]] - xu);
+            acc += bf[u] - ax;
+        }
+        bc[v] = acc;
+    }
+}
+
+// x_F[u] += omega x_C[parent of u].
+template <class T>
+__device__ __forceinline__ void gprolong(const MGLev& F, const MGLev& C, T omega, long long t0, long long nt) {
+    T* __restrict__ xf = (T*)F.x;
+    const T* __restrict__ xc = (const T*)C.x;
+    for (long long u = t0; u < F.M; u += nt) xf[u] = xf[u] + omega * xc[F.parent[u]];
+}
+
+// Coarsest level, one block: x = 0, then `sweeps` red-black passes and as many black-red (a
+// symmetric operator).  The iterate stays in global memory; __syncthreads orders the passes.
+template <class T>
+__device__ __forceinline__ void gcoarsest(const MGLev& L, int sweeps) {
+    T* x = (T*)L.x;
+    for (long long u = threadIdx.x; u < L.M; u += blockDim.x) x[u] = (T)0;
+    __syncthreads();
+    for (int pass = 0; pass < 4 * sweeps; ++pass) {
+        const int half = pass / (2 * sweeps);
+        gsmooth<T>(L, (pass & 1) ^ half, false, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gsmooth(MGLev L, int col, int zero, const SolveScal* sc) {
+    if (sc->done) return;
+    gsmooth<T>(L, col, zero != 0, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_grestrict(MGLev F, MGLev C, const SolveScal* sc) {
+    if (sc->done) return;
+    grestrict<T>(F, C, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gprolong(MGLev F, MGLev C, T omega, const SolveScal* sc) {
+    if (sc->done) return;
+    gprolong<T>(F, C, omega, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_gcoarsest(MGLev L, int sweeps, const SolveScal* sc) {
+    if (sc->done) return;
+    gcoarsest<T>(L, sweeps);
+}
+
+// The small levels first .. nlev-1 of a V-cycle in one launch: one cluster of MG_TAIL_CTAS blocks of
+// 1024 threads walks the descent (smoothing, restriction), the coarsest solve (block 0) and the
+// ascent (prolongation, smoothing), with a cluster barrier (hardware, release/acquire at cluster
+// scope) between dependent passes.  These levels are small and stay in L2; as separate kernels each
+// pass would cost a launch for a few microseconds of work.
+template <class T>
+__global__ void __launch_bounds__(1024) k_mg_tail(MGTail M, const SolveScal* sc) {
+    if (sc->done) return;                       // the flag is uniform: set by an earlier kernel
+    cg::cluster_group cl = cg::this_cluster();
+    const long long t0 = (long long)cl.block_rank() * blockDim.x + threadIdx.x;
+    const long long nt = (long long)cl.num_blocks() * blockDim.x;
+    auto bar = [&]() {
+        __threadfence();
+        cl.sync();
+    };
+    const int last = M.nlev - 1;
+    for (int l = M.first; l < last; ++l) {
+        for (int q = 0; q < M.sweeps; ++q) {
+            gsmooth<T>(M.lev[l], 0, q == 0, t0, nt);
+            bar();
+            gsmooth<T>(M.lev[l], 1, false, t0, nt);
+            bar();
+        }
+        grestrict<T>(M.lev[l], M.lev[l + 1], t0, nt);
+        bar();
+    }
+    if (cl.block_rank() == 0) gcoarsest<T>(M.lev[last], M.coarse_sweeps);
+    bar();
+    for (int l = last - 1; l >= M.first; --l) {
+        gprolong<T>(M.lev[l], M.lev[l + 1], (T)M.omega, t0, nt);
+        bar();
+        for (int q = 0; q < M.sweeps; ++q) {
+            gsmooth<T>(M.lev[l], 1, false, t0, nt);
+            bar();
+            gsmooth<T>(M.lev[l], 0, false, t0, nt);
+            bar();
+        }
+    }
+}
+
+// ---- transfer between the fine grid and level 1 -------------------------------------------------
+
+// b_1 of each part of a level-1 block = the sum of the fine residuals  scale r - (A z)  of its cells.
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_restrict0(Dom D, const T* __restrict__ r, const T* __restrict__ z, T scale,
+                                                      MGLev C, const SolveScal* sc) {
+    if (sc->done) return;
+    T* __restrict__ bc = (T*)C.b;
+    auto zv = [&](long long c) { return z[c]; };
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.P; q += (long long)gridDim.x * blockDim.x) {
+        int X[3];
+        coords3(q, C.px, C.py, X);
+        unsigned fl[8];
+        long long P[8];
+        const unsigned in = block_flags(D, X, fl, P);
+        int part[8];
+        const int np = fine_parts(D, fl, in, part);
+        T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (!((in >> m) & 1u)) continue;
+            const int x0 = 2 * X[0] + (m & 1), x1 = 2 * X[1] + ((m >> 1) & 1), x2 = 2 * X[2] + (m >> 2);
+            const T res = scale * r[P[m]] - link_sum7<T>(D, P[m], x0, x1, x2, fl[m], z[P[m]], zv);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) acc[s] += part[m] == s ? res : (T)0;
+        }
+        const int o = C.off[q];
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (s < np) bc[o + s] = acc[s];
+    }
+}
+
+// z += omega x_1(part of the cell).
+template <class T>
+__global__ void __launch_bounds__(256) k_mg_prolong0(Dom D, T* __restrict__ z, MGLev C, T omega, const SolveScal* sc) {
+    if (sc->done) return;
+    const T* __restrict__ xc = (const T*)C.x;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < C.P; q += (long long)gridDim.x * blockDim.x) {
+        int X[3];
+        coords3(q, C.px, C.py, X);
+        unsigned fl[8];
+        long long P[8];
+        const unsigned in = block_flags(D, X, fl, P);
+        int part[8];
+        const int np = fine_parts(D, fl, in, part);
+        const int o = C.off[q];
+        T v[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = s < np ? xc[o + s] : (T)0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            if (!((in >> m) & 1u)) continue;
+            T w = v[0];
+#pragma unroll
+            for (int s = 1; s < 8; ++s) w = part[m] == s ? v[s] : w;
+            z[P[m]] = z[P[m]] + omega * w;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ unsigned flags4(const Dom& D, long long P) {
+    return D.flags ? *reinterpret_cast<const unsigned*>(D.flags + P) : 0u;
+}
+
+// FP32 restriction with nx a multiple of 4: one thread per pair of level-1 positions (2 xp, 2 xp + 1)
+// at (Y, Z), i.e. the 4 fine cells [4 xp, 4 xp + 4) of each of the (up to) 4 fine rows below them,
+// with 16-byte loads.
+__global__ void __launch_bounds__(256) k_mg_restrict0_x4(Dom D, const float* __restrict__ r,
+                                                         const float* __restrict__ z, float scale, MGLev C,
+                                                         const SolveScal* sc) {
+    if (sc->done) return;
+    float* __restrict__ bc = (float*)C.b;
+    const int px = D.nx / 4;
+    const long long npairs = (long long)px * C.py * C.pz;
+    auto zv = [&](long long c) { return z[c]; };
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const unsigned tu = (unsigned)t, rq = tu / (unsigned)px;
+        const int xp = (int)(tu - rq * (unsigned)px), Y = (int)(rq % (unsigned)C.py), Z = (int)(rq / (unsigned)C.py);
+        const int i0 = 4 * xp;
+        float res[2][2][4];
+        unsigned f4[2][2];
+        unsigned rows = 0;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj) {
+                const int j = 2 * Y + dj, k = 2 * Z + dk;
+                f4[dk][dj] = 0u;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) res[dk][dj][m] = 0.f;
+                if (j >= D.ny || k >= D.nz) continue;
+                rows |= 1u << (2 * dk + dj);
+                const long long P = i0 + (long long)D.sy * j + D.sz * k;
+                const unsigned fl4 = flags4(D, P);
+                f4[dk][dj] = fl4;
+                const float4 r4 = ld4(r + P), z4 = ld4(z + P);
+                const float zc[4] = {z4.x, z4.y, z4.z, z4.w}, rr[4] = {r4.x, r4.y, r4.z, r4.w};
+                if (fl4 == 0u && i0 > 0 && i0 + 4 < D.nx && j > 0 && j < D.ny - 1 && k > 0 && k < D.nz - 1) {
+                    const float4 ym = ld4(z + P - D.sy), yp = ld4(z + P + D.sy);
+                    const float4 zm = ld4(z + P - D.sz), zp = ld4(z + P + D.sz);
+                    const float xl = z[P - 1], xr = z[P + 4];
+                    const float a[4] = {ym.x + yp.x + zm.x + zp.x, ym.y + yp.y + zm.y + zp.y,
+                                        ym.z + yp.z + zm.z + zp.z, ym.w + yp.w + zm.w + zp.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float xm = m == 0 ? xl : zc[m - 1];
+                        const float xq = m == 3 ? xr : zc[m + 1];
+                        res[dk][dj][m] = scale * rr[m] - ((xm + xq) + a[m] - 6.f * zc[m]);
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
+                        res[dk][dj][m] = scale * rr[m] - link_sum7<float>(D, P + m, i0 + m, j, k, fl, zc[m], zv);
+                    }
+                }
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned fl[8];
+            unsigned in = 0;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int di = m & 1, dj = (m >> 1) & 1, dk = m >> 2;
+                fl[m] = (f4[dk][dj] >> (8 * (2 * h + di))) & 0xffu;
+                in |= ((rows >> (2 * dk + dj)) & 1u) << m;
+            }
+            int part[8];
+            const int np = fine_parts(D, fl, in, part);
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float v = res[m >> 2][(m >> 1) & 1][2 * h + (m & 1)];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) acc[s] += part[m] == s ? v : 0.f;
+            }
+            const int o = C.off[(2 * xp + h) + (long long)C.px * (Y + (long long)C.py * Z)];
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (s < np) bc[o + s] = acc[s];
+        }
+    }
+}
+
+// FP32 prolongation with nx a multiple of 4, same layout as k_mg_restrict0_x4.
+__global__ void __launch_bounds__(256) k_mg_prolong0_x4(Dom D, float* __restrict__ z, MGLev C, float omega,
+                                                        const SolveScal* sc) {
+    if (sc->done) return;
+    const float* __restrict__ xc = (const float*)C.x;
+    const int px = D.nx / 4;
+    const long long npairs = (long long)px * C.py * C.pz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
+         t += (long long)gridDim.x * blockDim.x) {
+        const unsigned tu = (unsigned)t, rq = tu / (unsigned)px;
+        const int xp = (int)(tu - rq * (unsigned)px), Y = (int)(rq % (unsigned)C.py), Z = (int)(rq / (unsigned)C.py);
+        const int i0 = 4 * xp;
+        unsigned f4[2][2];
+        unsigned rows = 0;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj) {
+                const int j = 2 * Y + dj, k = 2 * Z + dk;
+                const bool ok = j < D.ny && k < D.nz;
+                f4[dk][dj] = ok ? flags4(D, i0 + (long long)D.sy * j + D.sz * k) : 0u;
+                rows |= (ok ? 1u : 0u) << (2 * dk + dj);
+            }
+        float w[2][8];     // [position][cell]: the coarse value each fine cell receives
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned fl[8];
+            unsigned in = 0;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int di = m & 1, dj = (m >> 1) & 1, dk = m >> 2;
+                fl[m] = (f4[dk][dj] >> (8 * (2 * h + di))) & 0xffu;
+                in |= ((rows >> (2 * dk + dj)) & 1u) << m;
+            }
+            int part[8];
+            const int np = fine_parts(D, fl, in, part);
+            const int o = C.off[(2 * xp + h) + (long long)C.px * (Y + (long long)C.py * Z)];
+            float v[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) v[s] = s < np ? xc[o + s] : 0.f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                float a = v[0];
+#pragma unroll
+                for (int s = 1; s < 8; ++s) a = part[m] == s ? v[s] : a;
+                w[h][m] = a;
+            }
+        }
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj) {
+                if (!((rows >> (2 * dk + dj)) & 1u)) continue;
+                const long long P = i0 + (long long)D.sy * (2 * Y + dj) + D.sz * (2 * Z + dk);
+                float4 z4 = ld4(z + P);
+                const int m0 = 2 * dj + 4 * dk;
+                z4.x += omega * w[0][m0];
+                z4.y += omega * w[0][m0 + 1];
+                z4.z += omega * w[1][m0];
+                z4.w += omega * w[1][m0 + 1];
+                st4(z + P, z4);
+            }
+    }
+}
+
 unsigned lin_blocks(long long n) {
     long long b = (n + 255) / 256;
     long long cap = 8LL * IBM_NSM;
@@ -456,30 +844,187 @@ unsigned lin_blocks(long long n) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-}  // namespace
+// ---- host side of the set-up --------------------------------------------------------------------
 
-int mg_levels_for(int nx, int ny, int nz, int dims[][3], int maxlev) {
-    int n = 0;
-    int d[3] = {nx, ny, nz};
-    for (;;) {
-        dims[n][0] = d[0];
-        dims[n][1] = d[1];
-        dims[n][2] = d[2];
-        ++n;
-        const long long cells = (long long)d[0] * d[1] * d[2];
-        if (n == maxlev || cells <= 1024 || (d[0] == 1 && d[1] == 1 && d[2] == 1)) break;
-        for (int a = 0; a < 3; ++a) d[a] = (d[a] + 1) / 2;
+struct SetupTmp {
+    long long* tiles = nullptr;     // scan tiles + 4 totals
+    long long nt = 0;
+    int* ovf = nullptr;
+    uint8_t* sub0 = nullptr;
+    ~SetupTmp() {
+        cudaFree(tiles);
+        cudaFree(ovf);
+        cudaFree(sub0);
     }
-    return n;
+};
+
+void free_level(MGLev& L) {
+    cudaFree(L.off); cudaFree(L.cnt); cudaFree(L.pos); cudaFree(L.rp); cudaFree(L.col); cudaFree(L.g);
+    cudaFree(L.d); cudaFree(L.invdg); cudaFree(L.parent); cudaFree(L.cp); cudaFree(L.ch); cudaFree(L.b);
+    cudaFree(L.x);
+    const int px = L.px, py = L.py, pz = L.pz;
+    const long long P = L.P;
+    memset(&L, 0, sizeof(L));
+    L.px = px; L.py = py; L.pz = pz; L.P = P;
 }
 
-int mg_setup(const LesCtx& c, MG& mg, cudaStream_t s) {
-    if (mg.nlev < 2) return IBM_OK;
-    k_mg_build1<<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, mg.lev[1]);
-    for (int l = 1; l + 1 < mg.nlev; ++l)
-        k_mg_build_next<<<lin_blocks(mg.lev[l + 1].N), 256, 0, s>>>(mg.lev[l], mg.lev[l + 1]);
-    for (int l = 1; l < mg.nlev; ++l) k_mg_invdiag<<<lin_blocks(mg.lev[l].N), 256, 0, s>>>(mg.lev[l]);
-    IBM_LAUNCHED("mg_setup");
+#define MG_ALLOC(ptr, n)                                                                         \
+    do {                                                                                         \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), ((n) > 0 ? (size_t)(n) : 1) * sizeof(*(ptr))); \
+        if (e_ != cudaSuccess) return ibm_cuda_check(e_, "multigrid set-up: " #ptr);              \
+    } while (0)
+#define MG_ALLOCB(ptr, bytes)                                                                    \
+    do {                                                                                         \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (size_t)(bytes) > 0 ? (size_t)(bytes) : 16); \
+        if (e_ != cudaSuccess) return ibm_cuda_check(e_, "multigrid set-up: " #ptr);              \
+    } while (0)
+
+long long read_ll(const long long* d) {
+    long long h = 0;
+    cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    return h;
+}
+
+// Colour-major offsets of the positions' unknowns; sets L.M0 and L.M.
+int number_unknowns(MGLev& L, SetupTmp& t) {
+    long long* tot = t.tiles + t.nt;
+    IBM_CUDA(scan_emit(L.P, PosCount{L.cnt, L.px, L.py, 0}, PosEmit{L.off, L.px, L.py, 0, nullptr}, t.tiles, tot, 0));
+    IBM_CUDA(scan_emit(L.P, PosCount{L.cnt, L.px, L.py, 1}, PosEmit{L.off, L.px, L.py, 1, tot}, t.tiles, tot + 1, 0));
+    IBM_CUDA(cudaDeviceSynchronize());
+    L.M0 = read_ll(tot);
+    L.M = L.M0 + read_ll(tot + 1);
+    if (L.M >= (1LL << 31)) return ibm_fail(IBM_E_INVALID, "multigrid set-up: too many unknowns");
+    return IBM_OK;
+}
+
+// Exclusive scan of a[0..n) in place; a[n] = total.  Returns the total in *total.
+int scan_in_place(int32_t* a, long long n, SetupTmp& t, long long* total) {
+    long long* tot = t.tiles + t.nt + 2;
+    IBM_CUDA(scan_emit(n, ArrCount{a}, ArrEmit{a}, t.tiles, tot, 0));
+    IBM_CUDA(cudaDeviceSynchronize());
+    *total = read_ll(tot);
+    if (*total >= (1LL << 31)) return ibm_fail(IBM_E_INVALID, "multigrid set-up: too many links");
+    const int32_t h = (int32_t)*total;
+    IBM_CUDA(cudaMemcpy(a + n, &h, sizeof(h), cudaMemcpyHostToDevice));
+    return IBM_OK;
+}
+
+int build_level1(const LesCtx& c, MGLev& L, int sb, SetupTmp& t) {
+    const Dom& D = c.D;
+    L.px = (D.nx + 1) / 2;
+    L.py = (D.ny + 1) / 2;
+    L.pz = (D.nz + 1) / 2;
+    L.P = (long long)L.px * L.py * L.pz;
+    MG_ALLOC(L.off, L.P);
+    MG_ALLOC(L.cnt, L.P);
+    k_parts1<<<lin_blocks(L.P), 256>>>(D, L, t.sub0);
+    IBM_LAUNCHED("k_parts1");
+    int rc = number_unknowns(L, t);
+    if (rc) return rc;
+    MG_ALLOC(L.pos, L.M);
+    MG_ALLOC(L.rp, L.M + 1);
+    MG_ALLOC(L.d, L.M);
+    MG_ALLOC(L.invdg, L.M);
+    MG_ALLOC(L.parent, L.M);
+    MG_ALLOCB(L.b, L.M * sb);
+    MG_ALLOCB(L.x, L.M * sb);
+    IBM_CUDA(cudaMemset(t.ovf, 0, sizeof(int)));
+    k_links1<<<lin_blocks(L.P), 256>>>(D, L, t.sub0, 0, t.ovf);
+    IBM_LAUNCHED("k_links1");
+    if ((rc = scan_in_place(L.rp, L.M, t, &L.nnz))) return rc;
+    MG_ALLOC(L.col, L.nnz);
+    MG_ALLOC(L.g, L.nnz);
+    k_links1<<<lin_blocks(L.P), 256>>>(D, L, t.sub0, 1, t.ovf);
+    IBM_LAUNCHED("k_links1");
+    IBM_CUDA(cudaDeviceSynchronize());
+    int h = 0;
+    IBM_CUDA(cudaMemcpy(&h, t.ovf, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return ibm_fail(IBM_E_INVALID, "multigrid set-up: a level-1 block has too many links");
+    return IBM_OK;
+}
+
+// Level C from level F; returns 1 (and leaves C empty) when the level would not shrink enough or
+// a row would not fit, 0 when built, < 0 on error (negated status).
+int build_next(MGLev& F, MGLev& C, int sb, SetupTmp& t) {
+    C.px = (F.px + 1) / 2;
+    C.py = (F.py + 1) / 2;
+    C.pz = (F.pz + 1) / 2;
+    C.P = (long long)C.px * C.py * C.pz;
+    MG_ALLOC(C.off, C.P);
+    MG_ALLOC(C.cnt, C.P);
+    k_parts_next<<<lin_blocks(C.P), 256>>>(F, C);
+    IBM_LAUNCHED("k_parts_next");
+    int rc = number_unknowns(C, t);
+    if (rc) return -rc;
+    if (C.M > (F.M * 4) / 5) {
+        free_level(C);
+        return 1;
+    }
+    k_parent_next<<<lin_blocks(F.M), 256>>>(F, C);
+    IBM_LAUNCHED("k_parent_next");
+    MG_ALLOC(C.pos, C.M);
+    MG_ALLOC(C.rp, C.M + 1);
+    MG_ALLOC(C.cp, C.M + 1);
+    MG_ALLOC(C.ch, F.M);
+    MG_ALLOC(C.d, C.M);
+    MG_ALLOC(C.invdg, C.M);
+    MG_ALLOC(C.parent, C.M);
+    MG_ALLOCB(C.b, C.M * sb);
+    MG_ALLOCB(C.x, C.M * sb);
+    IBM_CUDA(cudaMemset(t.ovf, 0, sizeof(int)));
+    k_links_next<<<lin_blocks(C.P), 256>>>(F, C, 0, t.ovf);
+    IBM_LAUNCHED("k_links_next");
+    IBM_CUDA(cudaDeviceSynchronize());
+    int h = 0;
+    IBM_CUDA(cudaMemcpy(&h, t.ovf, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        free_level(C);
+        return 1;
+    }
+    long long nch = 0;
+    if ((rc = scan_in_place(C.rp, C.M, t, &C.nnz))) return -rc;
+    if ((rc = scan_in_place(C.cp, C.M, t, &nch))) return -rc;
+    if (nch != F.M) return -ibm_fail(IBM_E_INVALID, "multigrid set-up: children do not cover the level");
+    MG_ALLOC(C.col, C.nnz);
+    MG_ALLOC(C.g, C.nnz);
+    k_links_next<<<lin_blocks(C.P), 256>>>(F, C, 1, t.ovf);
+    IBM_LAUNCHED("k_links_next");
+    IBM_CUDA(cudaDeviceSynchronize());
+    return 0;
+}
+
+}  // namespace
+
+void mg_free(MG& mg) {
+    for (int l = 1; l < IBM_MG_MAXLEV; ++l) free_level(mg.lev[l]);
+    mg.nlev = 1;
+}
+
+int mg_setup(const LesCtx& c, MG& mg, int sb) {
+    for (int l = 0; l < IBM_MG_MAXLEV; ++l) memset(&mg.lev[l], 0, sizeof(MGLev));
+    MGLev& L0 = mg.lev[0];
+    L0.px = c.D.nx;
+    L0.py = c.D.ny;
+    L0.pz = c.D.nz;
+    L0.P = L0.M = c.D.N;
+    mg.nlev = 1;
+    if (c.D.N <= MG_COARSE_TARGET) return IBM_OK;      // fine smoothing alone
+    SetupTmp t;
+    t.nt = scan_tiles(c.D.N);
+    MG_ALLOC(t.tiles, t.nt + 4);
+    MG_ALLOC(t.ovf, 1);
+    MG_ALLOC(t.sub0, c.D.N);
+    int rc = build_level1(c, mg.lev[1], sb, t);
+    if (rc) return rc;
+    mg.nlev = 2;
+    for (int l = 1; l + 1 < IBM_MG_MAXLEV; ++l) {
+        MGLev& F = mg.lev[l];
+        if (F.M <= MG_COARSE_TARGET || F.P == 1) break;
+        const int r2 = build_next(F, mg.lev[l + 1], sb, t);
+        if (r2 < 0) return -r2;
+        if (r2 > 0) break;
+        mg.nlev = l + 2;
+    }
     return IBM_OK;
 }
 
@@ -512,12 +1057,13 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
         fine(1, 0);
     }
     if (mg.nlev > 1) {
+        const MGLev& L1 = mg.lev[1];
         prof_begin(c.prof, PS_MG_TRANSFER, s);
         if constexpr (std::is_same<T, float>::value) {
-            if (vec) launch_mg_restrict0_x4(c, r, z, scale, mg.lev[1], sc, s);
-            else k_mg_restrict0<T><<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, r, z, scale, mg.lev[1], sc);
+            if (vec) k_mg_restrict0_x4<<<lin_blocks((c.D.nx / 4) * (long long)L1.py * L1.pz), 256, 0, s>>>(c.D, r, z, scale, L1, sc);
+            else k_mg_restrict0<T><<<lin_blocks(L1.P), 256, 0, s>>>(c.D, r, z, scale, L1, sc);
         } else {
-            k_mg_restrict0<T><<<lin_blocks(mg.lev[1].N), 256, 0, s>>>(c.D, r, z, scale, mg.lev[1], sc);
+            k_mg_restrict0<T><<<lin_blocks(L1.P), 256, 0, s>>>(c.D, r, z, scale, L1, sc);
         }
         prof_end(c.prof, PS_MG_TRANSFER, s);
         ++launches;
@@ -525,21 +1071,21 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
         // levels >= tf (if any) run in one cluster launch; separate kernels above them
         int tf = mg.nlev;
         for (int l = 1; l + 1 < mg.nlev; ++l)
-            if (mg.lev[l].N <= MG_TAIL_MAX_CELLS) { tf = l; break; }
+            if (mg.lev[l].M <= MG_TAIL_MAX) { tf = l; break; }
         const int top = tf < mg.nlev ? tf : mg.nlev - 1;
         for (int l = 1; l < top; ++l) {
             const MGLev& L = mg.lev[l];
             for (int q = 0; q < SC; ++q) {
-                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, q == 0, sc);
-                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
+                k_gsmooth<T><<<lin_blocks(q == 0 ? L.M : L.M0), 256, 0, s>>>(L, 0, q == 0, sc);
+                k_gsmooth<T><<<lin_blocks(L.M - L.M0), 256, 0, s>>>(L, 1, 0, sc);
                 launches += 2;
             }
-            k_mg_restrictc<T><<<lin_blocks(mg.lev[l + 1].N), 256, 0, s>>>(L, mg.lev[l + 1], sc);
+            k_grestrict<T><<<lin_blocks(mg.lev[l + 1].M), 256, 0, s>>>(L, mg.lev[l + 1], sc);
             ++launches;
         }
         if (tf < mg.nlev) {
             MGTail M;
-            for (int l = 0; l < mg.nlev; ++l) M.lev[l] = mg.lev[l];
+            for (int l = 0; l < IBM_MG_MAXLEV; ++l) M.lev[l] = mg.lev[l];
             M.first = tf;
             M.nlev = mg.nlev;
             M.sweeps = SC;
@@ -560,22 +1106,27 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
             IBM_CUDA(cudaLaunchKernelEx(&cfg, k_mg_tail<T>, M, (const SolveScal*)sc));
             ++launches;
         } else {
-            k_mg_coarsest<T><<<1, 1024, 0, s>>>(mg.lev[mg.nlev - 1], mg.coarse_sweeps, sc);
+            k_gcoarsest<T><<<1, 1024, 0, s>>>(mg.lev[mg.nlev - 1], mg.coarse_sweeps, sc);
             ++launches;
         }
         for (int l = top - 1; l >= 1; --l) {
             const MGLev& L = mg.lev[l];
-            k_mg_prolong<T><<<lin_blocks(L.N), 256, 0, s>>>(L.N, L.nx, L.ny, (T*)L.x, mg.lev[l + 1], om, sc);
+            k_gprolong<T><<<lin_blocks(L.M), 256, 0, s>>>(L, mg.lev[l + 1], om, sc);
             ++launches;
             for (int q = 0; q < SC; ++q) {
-                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 1, 0, sc);
-                k_mg_smoothc<T><<<lin_blocks((L.N + 1) / 2), 256, 0, s>>>(L, 0, 0, sc);
+                k_gsmooth<T><<<lin_blocks(L.M - L.M0), 256, 0, s>>>(L, 1, 0, sc);
+                k_gsmooth<T><<<lin_blocks(L.M0), 256, 0, s>>>(L, 0, 0, sc);
                 launches += 2;
             }
         }
         prof_end(c.prof, PS_MG_COARSE, s);
         prof_begin(c.prof, PS_MG_TRANSFER, s);
-        k_mg_prolong<T><<<lin_blocks(c.D.N), 256, 0, s>>>(c.D.N, c.D.nx, c.D.ny, z, mg.lev[1], om, sc);
+        if constexpr (std::is_same<T, float>::value) {
+            if (vec) k_mg_prolong0_x4<<<lin_blocks((c.D.nx / 4) * (long long)L1.py * L1.pz), 256, 0, s>>>(c.D, z, L1, om, sc);
+            else k_mg_prolong0<T><<<lin_blocks(L1.P), 256, 0, s>>>(c.D, z, L1, om, sc);
+        } else {
+            k_mg_prolong0<T><<<lin_blocks(L1.P), 256, 0, s>>>(c.D, z, L1, om, sc);
+        }
         prof_end(c.prof, PS_MG_TRANSFER, s);
         ++launches;
     }

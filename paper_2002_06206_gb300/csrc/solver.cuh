@@ -30,22 +30,34 @@ struct Prof {
 void prof_begin(Prof* p, int slot, cudaStream_t s);
 void prof_end(Prof* p, int slot, cudaStream_t s);
 
-// One level of the multigrid preconditioner (mg.cu).  Level 0 is the fine grid and keeps its links in
-// the flags; coarser levels store the conductance of each cell's +x, +y, +z link.
-#define IBM_MG_MAXLEV 12
+// One level of the multigrid preconditioner (mg.cu).  Level 0 is the fine grid (its links are in the
+// flags).  A position of level l >= 1 is a block of 2^l x 2^l x 2^l fine cells; its unknowns are the
+// connected parts of the block (connected through links inside the block), so an aggregate never
+// spans a wall.  Unknowns are numbered by colour (parity of the position), then position, then part;
+// the links of unknown u are col/g[rp[u] .. rp[u+1]).
+#define IBM_MG_MAXLEV 16
 struct MGLev {
-    int nx, ny, nz;
-    long long N, sy, sz;
-    int per[3];          // periodic axes
-    float* g[3];         // conductance of the +a link
-    float* d;            // Dirichlet (outflow) diagonal term
-    float* invdg;        // 1 / (sum of link conductances + d), 0 for an isolated cell
+    int px, py, pz;      // positions along x, y, z
+    long long P;         // positions
+    long long M, M0;     // unknowns; the first M0 have colour 0
+    long long nnz;       // stored links (each link once from either end)
+    int32_t* off;        // [P] first unknown of each position
+    int32_t* cnt;        // [P] unknowns (parts) of each position
+    int32_t* pos;        // [M] position of each unknown
+    int32_t* rp;         // [M + 1] first link of each unknown
+    int32_t* col;        // [nnz] neighbour unknown
+    float* g;            // [nnz] conductance: sum of the fine conductances between the two aggregates
+    float* d;            // [M] Dirichlet (outflow) diagonal term
+    float* invdg;        // [M] 1 / (sum of g + d), 0 for an isolated unknown
+    int32_t* parent;     // [M] unknown of level l + 1 that contains this one
+    int32_t* cp;         // [M + 1] first child (levels >= 2: children are unknowns of level l - 1)
+    int32_t* ch;         // [M of level l - 1] children, grouped by parent
     void* b;             // right-hand side (working precision)
-    void* x;             // iterate (working precision)
+    void* x;             // iterate
 };
 struct MG {
     int nlev;
-    int sweeps;          // red-black passes before and after the coarse correction, per level
+    int sweeps;          // red-black passes before and after the coarse correction on the fine grid
     int coarse_sweeps;   // symmetric sweeps on the coarsest level
     double omega;        // coarse-correction factor, 0 < omega < 2
     MGLev lev[IBM_MG_MAXLEV];
@@ -114,18 +126,17 @@ int launch_viscous_force(const LesCtx& c, const void* u, double* d_out4, cudaStr
 int launch_forces(const LesCtx& c, const float* tri, long long ntri, const double* p, double* d_out4,
                   cudaStream_t s);
 
-// poisson.cu
 // stencil4.cu: FP32 fine-grid kernels with 4 cells per thread (nx a multiple of 4)
-void launch_mg_restrict0_x4(const LesCtx& c, const float* r, const float* z, float scale, const MGLev& C,
-                            SolveScal* sc, cudaStream_t s);
 bool x4_ok(const LesCtx& c);
 void launch_cg_dir_spmv_x4(const LesCtx& c, const float* src, const float* pold, float* pnew, float* q, float idx2,
                            SolveScal* sc, int pcg, cudaStream_t s);
 void launch_mg_smooth0_x4(const LesCtx& c, const float* r, float* z, float scale, int col, int zero, int fin,
                           SolveScal* sc, cudaStream_t s);
 
-int mg_levels_for(int nx, int ny, int nz, int dims[][3], int maxlev);
-int mg_setup(const LesCtx& c, MG& mg, cudaStream_t s);
+// Builds the levels (allocates them; synchronises the device).  mg.sweeps, omega and coarse_sweeps
+// must be set; mg_free releases what mg_setup allocated (also after a failed set-up).
+int mg_setup(const LesCtx& c, MG& mg, int precision_bytes);
+void mg_free(MG& mg);
 template <class T>
 int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cudaStream_t s);
 

@@ -185,75 +185,9 @@ __global__ void __launch_bounds__(256, 4) k_mg_smooth0_x4(Dom D, const float* __
         });
 }
 
-// Level-0 residual restricted to level 1, one thread per pair of coarse cells (X0, X0 + 1) at (Y, Z):
-// the 4 fine cells [4 X0', 4 X0' + 4) of each of the (up to) 4 fine rows below them, with 16-byte
-// loads.  b_C = sum over the children of  scale r - (sum_links g (z_N - z_P) - d z_P).
-__global__ void __launch_bounds__(256) k_mg_restrict0_x4(Dom D, const float* __restrict__ r,
-                                                         const float* __restrict__ z, float scale, MGLev C,
-                                                         const SolveScal* sc) {
-    if (sc->done) return;
-    float* __restrict__ bc = (float*)C.b;
-    const int px = D.nx / 4;                                  // coarse-cell pairs along x
-    const long long npairs = (long long)px * C.ny * C.nz;
-    auto zv = [&](long long c) { return z[c]; };
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npairs;
-         t += (long long)gridDim.x * blockDim.x) {
-        const unsigned tu = (unsigned)t, rq = tu / (unsigned)px;
-        const int xp = (int)(tu - rq * (unsigned)px), Y = (int)(rq % (unsigned)C.ny), Z = (int)(rq / (unsigned)C.ny);
-        const int i0 = 4 * xp;
-        float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-        for (int dk = 0; dk < 2; ++dk)
-#pragma unroll
-            for (int dj = 0; dj < 2; ++dj) {
-                const int j = 2 * Y + dj, k = 2 * Z + dk;
-                if (j >= D.ny || k >= D.nz) continue;
-                const long long P = i0 + (long long)D.sy * j + D.sz * k;
-                const unsigned fl4 = flags4(D, P);
-                const float4 r4 = ld4(r + P), z4 = ld4(z + P);
-                float res[4];
-                if (plain_chunk(D, i0, j, k, fl4)) {
-                    const float4 ym = ld4(z + P - D.sy), yp = ld4(z + P + D.sy);
-                    const float4 zm = ld4(z + P - D.sz), zp = ld4(z + P + D.sz);
-                    const float xl = z[P - 1], xr = z[P + 4];
-                    const float zc[4] = {z4.x, z4.y, z4.z, z4.w}, rr[4] = {r4.x, r4.y, r4.z, r4.w};
-                    const float a[4] = {ym.x + yp.x + zm.x + zp.x, ym.y + yp.y + zm.y + zp.y,
-                                        ym.z + yp.z + zm.z + zp.z, ym.w + yp.w + zm.w + zp.w};
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const float xm = m == 0 ? xl : zc[m - 1];
-                        const float xq = m == 3 ? xr : zc[m + 1];
-                        const float az = (xm + xq) + a[m] - 6.f * zc[m];
-                        res[m] = scale * rr[m] - az;
-                    }
-                } else {
-                    const float zc[4] = {z4.x, z4.y, z4.z, z4.w}, rr[4] = {r4.x, r4.y, r4.z, r4.w};
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
-                        res[m] = scale * rr[m] - link_sum7<float>(D, P + m, i0 + m, j, k, fl, zc[m], zv);
-                    }
-                }
-                acc0 += res[0] + res[1];
-                acc1 += res[2] + res[3];
-            }
-        const long long q = 2 * xp + C.sy * Y + C.sz * Z;
-        bc[q] = acc0;
-        bc[q + 1] = acc1;
-    }
-}
-
 }  // namespace
 
 bool x4_ok(const LesCtx& c) { return (c.D.nx % 4) == 0; }
-
-void launch_mg_restrict0_x4(const LesCtx& c, const float* r, const float* z, float scale, const MGLev& C,
-                            SolveScal* sc, cudaStream_t s) {
-    const long long n = (long long)(c.D.nx / 4) * C.ny * C.nz;
-    long long b = (n + 255) / 256;
-    if (b > 8LL * IBM_NSM) b = 8LL * IBM_NSM;
-    k_mg_restrict0_x4<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(c.D, r, z, scale, C, sc);
-}
 
 dim3 x4_grid(const LesCtx& c) {
     const long long tiles = (long long)((c.D.nx / 4 + X4_TX - 1) / X4_TX) * ((c.D.ny + X4_TY - 1) / X4_TY) *
