@@ -2,9 +2,13 @@
 
 A step is one fractional time step of the whole hot path (CSM eddy viscosity, Crank-Nicolson predictor
 with 10 % QUICK and its momentum BiCGStab, IB forcing, face velocities, RHS, pressure solve to
-||b - A p|| / ||b|| <= 1e-6, correction) on the dirty sphere workload: 256 x 128 x 128 cells (4.19 M),
-a 40.6k-triangle dirty icosphere soup, FP32 stencils with FP64 iterative refinement of the pressure.
-The default warm-up of 400 steps puts the timed window at steps 401-500 of the run.
+||b - A p|| / ||b|| <= 1e-6 by multigrid-preconditioned CG, correction), FP32 stencils with FP64
+iterative refinement of the pressure.  The headline workload is the largest one that fits one GPU:
+the 1024 x 512 x 384 (201 M cells) vehicle-like assembly of ~2 M dirty triangles on a no-slip floor,
+with the dead-end filter on.  The same line carries the 512 x 256 x 256 cube-and-plate workload
+(plain and with the learned initial guess in the same window; the guess is trained on solver
+snapshots of the 256 x 128 x 128 dirty sphere), the pure-FP64 path (64 x 32 x 32 sphere, 50 steps to
+1e-10, and the cube-and-plate), and the oracle timed on the host cores.
 Metric: Mcell-steps/s = cells * steps / seconds.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -28,16 +32,33 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = "dirty_sphere_256x128x128"
+WORKLOAD = "vehicle_1024x512x384"
+SECONDARY = "cube_plate_512x256x256"
+TRAIN_WORKLOAD = "dirty_sphere_256x128x128"
+FP64_SMALL = "sphere_64x32x32"
 METRIC = "Mcell-steps/s at Poisson rel. residual 1e-6, learned+mixed vs plain, %HBM roof"
 UNIT = "Mcell-steps/s"
 FALLBACK_HBM = 6800.0
-# CG iterations per step the oracle is charged in its extrapolated step (about the GPU's measured
-# mean of multigrid-preconditioned CG on this workload)
-I_REF_DEFAULT = 20
+# CG iterations per step charged to the oracle's sample step (about the GPU's measured mean of
+# multigrid-preconditioned CG on the vehicle workload; the sample runs exactly this many)
+I_REF_DEFAULT = 30
 
-# algorithmic bytes per cell of each timed kernel group (s = bytes of a working-precision value)
-def bytes_per_cell(s, integrator="cn"):
+
+def bytes_per_cell(s, integrator="cn", sweeps=2, fused=False):
+    """Algorithmic bytes per cell of each timed kernel group (s = bytes of a working-precision value):
+    every array a pass needs is read once and every array it produces is written once."""
+    if fused:
+        # two launches per V-cycle: pre-smoothing + restriction reads r and the flags and writes z and
+        # b_1 (level 1 ~ N/8 values); post-smoothing + (r, z) reads r, z and the flags and writes z
+        mg_fine = ((2 * s + 1 + s / 8.0) + (3 * s + 1)) / 2.0
+        mg_transfer = 2 * s + 1 + (s + 4) / 8.0          # prolongation: z, flags, x_1, offsets -> z
+    else:
+        # fine-grid red-black passes of one V-cycle: the first reads r and the flags and writes z (z = 0
+        # before it); every other pass reads r, z and the flags and writes z (both colours share lines)
+        n_pass = 4 * sweeps
+        mg_fine = ((2 * s + 1) + (n_pass - 1) * (3 * s + 1)) / n_pass
+        # restriction (r, z, flags -> b_1) and prolongation (z, flags, x_1 -> z), level 1 ~ N/8 values
+        mg_transfer = 2 * s + 1 + (s + 4) / 8.0
     return {
         "csm": 4 * s + 1,                 # u (3) + flags -> nu_t
         # AB2: u, U, nu_t, Hprev, flags -> H, u*;  CN: u, U, nu_t, flags -> H, r, r_hat, delta
@@ -45,10 +66,11 @@ def bytes_per_cell(s, integrator="cn"):
         "faces": 6 * s + 1,               # u*, flags -> U*
         "rhs": 3 * s + 8,                 # U* -> b (fp64)
         "residual": 8 + 8 + 1 + s,        # b, x (fp64), flags -> r
-        "cg_dir_spmv": 4 * s + 1,         # r, p_old, flags -> p, q
+        "cg_dir_spmv": 4 * s + 1,         # z, p_old, flags -> p, q
         "cg_update": 6 * s,               # x, p, r, q -> x, r
         "correct": 12 * s + 9,            # u*, U*, p (fp64), flags -> u, U
-        "mg_fine": 2 * s + 1,             # one red-black colour pass: z (all), r and z (one colour), flags
+        "mg_fine": mg_fine,
+        "mg_transfer": mg_transfer,
     }
 
 
@@ -56,7 +78,8 @@ def bytes_per_cell(s, integrator="cn"):
 GROUP_KERNEL = {"csm": "k_csm", "predict": "k_cn_begin (tiled + general)", "faces": "k_faces",
                 "rhs": "k_rhs", "residual": "k_residual", "cg_dir_spmv": "k_cg_dir_spmv_x4",
                 "cg_update": "k_cg_update", "correct": "k_correct_cells + k_correct_faces",
-                "mg_fine": "k_mg_smooth0_x4"}
+                "mg_fine": "k_mg_smooth0_x4", "mg_transfer": "k_mg_restrict0_x4 + k_mg_prolong0_x4"}
+GROUP_KERNEL_FUSED = {"mg_fine": "k_mg_pre_fused + k_mg_post_fused", "mg_transfer": "k_mg_prolong0_x4"}
 
 
 def read_peaks():
@@ -79,15 +102,17 @@ def src_hash(files=None):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if the sources that define that kernel
-    (the files listed with it) are unchanged since the capture."""
+def ncu_traffic(kernel_key, workload=WORKLOAD):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this workload and the
+    sources that define that kernel (the files listed with it) are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         with open(path) as f:
             d = json.load(f)
         k = d["kernels"].get(kernel_key)
         if not k or k.get("source_hash") != src_hash(k["files"]):
+            return None
+        if k.get("workload", workload) != workload:
             return None
         return k.get("dram_bytes_per_launch_full_size")
     except Exception:
@@ -104,7 +129,7 @@ class Clocks:
     def __init__(self, gpu_id):
         self.gpu_id = gpu_id
         self.proc = None
-        self.path = os.path.join("/tmp", "bench_clocks_%d_%d.csv" % (os.getpid(), int(time.time())))
+        self.path = os.path.join("/tmp", "bench_clocks_%d_%d.csv" % (os.getpid(), int(time.time() * 1e3)))
 
     def __enter__(self):
         try:
@@ -171,81 +196,138 @@ def barrier(world):
         dist.barrier()
 
 
-# ------------------------------------------------------------------------------------------------
-# CPU baseline: the oracle as it stands, on a bounded sample of the same workload
+def workload_config(name, args, precision="fp32"):
+    """The static description of a workload (the same dict in both arms of the benchmark)."""
+    cfg = W.get_config(name)
+    return {"workload": name, "cells": cfg.ncell, "grid": [cfg.nx, cfg.ny, cfg.nz],
+            "precision": "fp32 stencils and cg, fp64 residual refinement" if precision == "fp32" else "fp64",
+            "solver": "cg + connected-part multigrid V-cycle" if args.precond == "mg" else "cg",
+            "tol": cfg.tol if precision == "fp32" else 1e-10,
+            "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
+            "quick": args.quick, "mg_sweeps": args.mg_sweeps, "mg_omega": args.mg_omega,
+            "deadend_filter": bool(cfg.deadend_on), "parallelism": "single",
+            "l2": "state far larger than L2 (tens of GB vs 126 MB); no flush needed"
+            if cfg.ncell >= 33554432 else "state larger than L2 (~0.4 GB vs 126 MB)"}
 
-def oracle_sample(cfg, iters_per_step, n_iter_sample=5, planes=8, integrator="cn", quick=0.1, mom_tol=1e-6):
-    """Time the FP64 oracle on a z-slab of the workload (the `planes` planes through the body's centre,
-    same soup, same per-cell work) -- one pass of every non-Poisson operator (the Crank-Nicolson
-    predictor with its momentum BiCGStab, or the AB2 predictor) plus n_iter_sample CG iterations -- and
-    scale to one full-size step: t = (N / N_slab) * (t_ops + I * t_iter)."""
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on bounded samples of the same workload
+
+def _slab_case(cfg, planes, k0, quick):
     import oracle
-    k0 = cfg.nz // 2 - planes // 2
     tri = cfg.soup().copy()
     tri[..., 2] -= k0
     case = oracle.Case(cfg.nx, cfg.ny, planes, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
                        cfg.forcing_on, cfg.deadend_on, quick)
     case.set_geometry(tri)
     u = W.initial_fields(W.Config("slab", cfg.nx, cfg.ny, planes, 0, 0, 0, 0, 0, cfg.bc, seed=cfg.seed)).reshape(-1)
-    U = case.faces(u)
+    return case, u
+
+
+def slab_k0(cfg, planes):
+    """First plane of the sample slab: through the bodies (a quarter of the height on a floor, the
+    middle otherwise)."""
+    if cfg.bc[4] == 4:                          # no-slip floor
+        return max(0, min(cfg.nz - planes, cfg.nz // 4 - planes // 2))
+    return cfg.nz // 2 - planes // 2
+
+
+class OracleSample:
+    """An oracle step on a z-slab of a workload (`planes` planes): CSM, the Crank-Nicolson predictor with
+    its momentum BiCGStab (or AB2), forcing, faces, RHS, exactly `iters` CG iterations of the pressure
+    solve, correction -- the per-cell work of a full step.  The slab is classified once; every step()
+    starts from the same initial field and times the step alone."""
+
+    def __init__(self, name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6):
+        cfg = W.get_config(name)
+        self.k0 = slab_k0(cfg, planes) if k0 is None else k0
+        self.case, self.u = _slab_case(cfg, planes, self.k0, quick)
+        self.iters, self.integrator, self.mom_tol, self.planes = int(iters), integrator, mom_tol, planes
+
+    def step(self):
+        import oracle
+        case, u = self.case, self.u
+        U = case.faces(u)
+        t0 = time.perf_counter()
+        nut = case.csm(u)
+        if self.integrator == "cn":
+            H, us, _ = case.predict_cn(u, U, nut, tol=self.mom_tol)
+        else:
+            H, us = case.predict(u, U, nut, np.zeros_like(u), True)
+        us2, _ = case.forcing(us)
+        Us = case.faces(us2)
+        b = case.rhs(Us)
+        p, st = case.solve(b, None, tol=1e-30, maxit=self.iters, solver=oracle.CG)
+        case.correct(us2, Us, p)
+        t1 = time.perf_counter()
+        return {"cells": case.N, "seconds": t1 - t0, "k0": self.k0, "planes": self.planes, "cg_iters": st.iters}
+
+
+def oracle_sample_step(name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6):
+    return OracleSample(name, iters, planes, k0, integrator, quick, mom_tol).step()
+
+
+def _sample_worker(args):
+    name, iters, planes, k0, integrator, quick = args
+    return oracle_sample_step(name, iters, planes, k0, integrator, quick)
+
+
+def oracle_full_run(name):
+    """The whole small workload on the oracle, as the workload defines it (every step to its tolerance
+    with the oracle's BiCGStab); returns (cells, steps, seconds)."""
+    import oracle
+    cfg = W.get_config(name)
+    case = oracle.Case.from_config(cfg)
+    case.set_geometry(cfg.soup())
+    st = case.initial_state(W.initial_fields(cfg))
     t0 = time.perf_counter()
-    nut = case.csm(u)
-    if integrator == "cn":
-        H, us, mom_it = case.predict_cn(u, U, nut, tol=mom_tol)
-    else:
-        H, us = case.predict(u, U, nut, np.zeros_like(u), True)
-    us2, _ = case.forcing(us)
-    Us = case.faces(us2)
-    b = case.rhs(Us)
-    t1 = time.perf_counter()
-    p, st = case.solve(b, None, tol=1e-30, maxit=n_iter_sample, solver=oracle.CG)
-    t2 = time.perf_counter()
-    case.correct(us2, Us, p)
-    t3 = time.perf_counter()
-    t_ops = (t1 - t0) + (t3 - t2)
-    t_iter = (t2 - t1) / max(st.iters, 1)
-    scale = cfg.ncell / case.N
-    t_step = scale * (t_ops + iters_per_step * t_iter)
-    sample = ("oracle (FP64, 1 thread) on the %dx%dx%d slab through the body centre: one pass of csm, %s "
-              "predictor, forcing, faces, rhs, correct plus %d CG iterations; full step = (N/N_slab) * "
-              "(t_ops + I * t_iter) with I = %.1f CG iterations per step"
-              % (cfg.nx, cfg.ny, planes, "Crank-Nicolson (momentum BiCGStab to %g)" % mom_tol if integrator == "cn"
-                 else "AB2", st.iters, iters_per_step))
-    return {"t_step_s": t_step, "t_ops_s": t_ops * scale, "t_iter_s": t_iter * scale, "sample": sample,
-            "wall_s": t3 - t0}
+    for _ in range(cfg.steps):
+        case.step(st, tol=cfg.tol)
+    return cfg.ncell, cfg.steps, time.perf_counter() - t0
+
+
+def _full_run_worker(name):
+    return oracle_full_run(name)
+
+
+def _sample_desc(name, planes, iters, integrator):
+    cfg = W.get_config(name)
+    return ("oracle (FP64, plain C) step on a %dx%dx%d z-slab of %s: csm, %s predictor, forcing, faces, rhs, "
+            "%d CG iterations (about the GPU's multigrid-preconditioned count per step), correction; value = "
+            "slab cells / seconds of that step" % (cfg.nx, cfg.ny, planes, name,
+                                                   "Crank-Nicolson (momentum BiCGStab to 1e-6)" if integrator == "cn"
+                                                   else "AB2", iters))
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cfg = W.get_config(args.workload)
-    I = float(os.environ.get("IBM_REF_ITERS", I_REF_DEFAULT))
-    kw = dict(integrator=args.integrator, quick=args.quick)
-    # The oracle has nothing to warm up; one sample on an 8-plane slab stands for the W warm-up steps
-    # and sizes the K timed samples so that the whole run stays within about two minutes.
-    first = oracle_sample(cfg, I, planes=8, **kw)
-    budget_s = 120.0
-    planes = int(max(2, min(8, 8 * (budget_s / max(args.steps, 1)) / max(first["wall_s"], 1e-3))))
-    times = []
-    for _ in range(args.steps):
-        times.append(oracle_sample(cfg, I, planes=planes, **kw))
-    t_step = float(np.mean([t["t_step_s"] for t in times]))
-    value = cfg.ncell / t_step / 1e6
+    I = int(os.environ.get("IBM_REF_ITERS", I_REF_DEFAULT))
+    planes = 1 if W.get_config(args.workload).ncell > 50_000_000 else 2
+    sample = OracleSample(args.workload, I, planes, integrator=args.integrator, quick=args.quick)
+    for _ in range(args.warmup):
+        sample.step()
+    samples = [sample.step() for _ in range(args.steps)]
+    secs = float(sum(s["seconds"] for s in samples))
+    cells = samples[0]["cells"]
+    value = cells * args.steps / secs / 1e6
+    cores = 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": cfg.ncell,
-                       "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
-                       "quick": args.quick, "slab_planes": planes},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": times[0]["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": _sample_desc(args.workload, planes, I, args.integrator),
+                             "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------------------------------------
+# GPU measurements
 
-def time_classify(L, torch, name="vehicle_1024x512x384", repeats=5):
+def time_classify(L, torch, name=WORKLOAD, repeats=5):
     """ibm_classify on the vehicle-like assembly (separate from the step): median of `repeats` runs,
     in predicate tests per second; the soup and buffers are resident on the device."""
     import ctypes as C
@@ -291,42 +373,189 @@ def net_init(seed=0, scale=0.05):
     return np.concatenate([x * scale for x in w] + [np.zeros(17)]).astype(np.float32)
 
 
-def timed_steps(torch, solver, st, steps, stream):
+def make_solver(L, torch, name, args, precision=None, geo=None, own_scheme=False):
+    """Solver of a workload with the benchmark's scheme (Crank-Nicolson, QUICK blend), or with the
+    workload's own integrator and blend (own_scheme)."""
+    cfg = W.get_config(name)
+    integ = cfg.integrator if own_scheme else (1 if args.integrator == "cn" else 0)
+    quick = cfg.quick if own_scheme else args.quick
+    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
+    if geo is None:
+        geo = L.Geometry(g, torch.from_numpy(cfg.soup()).cuda(), deadend_on=cfg.deadend_on)
+    prec = cfg.precision if precision is None else precision
+    solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=prec, solver=L.CG,
+                      tol=cfg.tol if prec != L.FP64 else (cfg.tol if name == FP64_SMALL else 1e-10),
+                      max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
+                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo,
+                      precond=L.MULTIGRID if args.precond == "mg" else L.NO_PRECOND,
+                      quick=quick, integrator=L.CRANK_NICOLSON if integ == 1 else L.ADAMS_BASHFORTH,
+                      mg_sweeps=args.mg_sweeps, mg_omega=args.mg_omega)
+    return cfg, g, geo, solver
+
+
+def checked_step(L, solver, st, tol):
+    s = solver.step(st)
+    if s.status != 0 or not (s.relres <= tol):
+        raise RuntimeError("step failed: status %d, relres %.3e" % (s.status, s.relres))
+    return s
+
+
+def timed_steps(L, torch, solver, st, steps, tol, stream, clocks=None):
+    """K steps between CUDA events on the launching stream, inputs resident in HBM."""
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     stats = []
+    n0 = solver.kernel_launches()
     e0.record(stream)
     for _ in range(steps):
-        stats.append(solver.step(st).as_dict())
+        stats.append(checked_step(L, solver, st, tol).as_dict())
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1), stats
+    return e0.elapsed_time(e1), stats, solver.kernel_launches() - n0
 
 
-def run_learned(args, L, torch, solver, st, geo, cfg, world):
-    """Learned initial guess: snapshots (b, p^n, p^{n-1}, p^{n+1}) from the solver's own steps, Adam
-    training on the GPU with the library's kernels, then K steps without and K steps with the guess
-    from the same point of the run."""
+def solve_summary(stats):
+    return {"inner_iters_per_step": float(np.mean([s["iters"] for s in stats])),
+            "refinements_per_step": float(np.mean([s["outer"] for s in stats])),
+            "momentum_bicgstab_iters_per_step": float(np.mean([s["mom_iters"] for s in stats])),
+            "max_relres": float(max(s["relres"] for s in stats))}
+
+
+def kernel_groups(solver, torch, st, steps, N, s_bytes, args, tol, peak):
+    """The same number of steps again with per-kernel CUDA events recorded on the launching stream
+    (graphs off while the profiler is on): per group achieved GB/s = algorithmic bytes per launch /
+    mean launch time."""
+    solver.profile(1)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        s = solver.step(st)
+        if s.status != 0:
+            raise RuntimeError("profiled step failed: status %d" % s.status)
+    torch.cuda.synchronize()
+    prof = solver.profile_read()
+    solver.profile(0)
+    fused = solver.mg_info()[1]
+    bpc = bytes_per_cell(s_bytes, args.integrator, args.mg_sweeps, fused)
+    groups = {}
+    for k, (ms_k, n_k) in prof.items():
+        if n_k <= 0 or k not in bpc:
+            continue
+        gbs = bpc[k] * N / (ms_k / n_k * 1e-3) / 1e9
+        groups[k] = {"launches": n_k, "avg_launch_ms": ms_k / n_k, "bytes_per_launch": bpc[k] * N,
+                     "achieved_gbs": gbs, "frac": gbs / peak}
+    return prof, groups
+
+
+def measure(L, torch, name, args, world, stream, precision=None, steps=None, warmup=None, profile=True,
+            e2e_steps=0, clocks=False, own_scheme=False):
+    """Warm-up, then K timed steps; optionally the per-kernel profile pass and the end-to-end pass."""
+    cfg, g, geo, solver = make_solver(L, torch, name, args, precision, own_scheme=own_scheme)
+    tol = solver.params.tol
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    st = solver.fields(W.initial_fields(cfg))
+    for _ in range(warmup):
+        checked_step(L, solver, st, tol)
+    torch.cuda.synchronize()
+    barrier(world)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(torch.cuda.current_device())
+    clk = None
+    if clocks:
+        with Clocks(gpu_id) as c:
+            ms, stats, launches = timed_steps(L, torch, solver, st, steps, tol, stream)
+        clk = c.summary()
+    else:
+        ms, stats, launches = timed_steps(L, torch, solver, st, steps, tol, stream)
+    barrier(world)
+    ms = max_over_ranks(ms, world)
     N = cfg.ncell
-    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
-    stream = torch.cuda.current_stream()
+    out = {"workload": name, "cells": N, "value": N * steps * world / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "timed_steps": [warmup + 1, warmup + steps], "gpu_launches": launches,
+           "solve": solve_summary(stats), "clocks": clk}
+    s_bytes = 8 if solver.params.precision == L.FP64 else 4
+    if profile:
+        peak, peak_kind = read_peaks()
+        prof, groups = kernel_groups(solver, torch, st, steps, N, s_bytes, args, tol, peak)
+        everything = {k: v for k, v in prof.items() if v[1] > 0}
+        tot = sum(x[0] for x in everything.values())
+        out["shares"] = {k: round(v[0] / tot, 4) for k, v in everything.items()}
+        out["groups"] = groups
+        out["peak"] = (peak, peak_kind)
+        out["mg"] = dict(zip(("levels", "fused_fine_passes", "unknowns"), solver.mg_info()))
+        if args.integrator == "cn" and prof["momentum"][1] > 0:
+            # momentum BiCGStab per step: M iterations of (68 s + 2) bytes per cell (p update, two operator
+            # passes, s update, x/r update over the stacked 3N vector)
+            M = out["solve"]["momentum_bicgstab_iters_per_step"]
+            mb = M * (68 * s_bytes + 2) * N
+            mms = prof["momentum"][0] / steps
+            groups["momentum_per_step"] = {"launches": steps, "avg_launch_ms": mms, "bytes_per_launch": mb,
+                                           "achieved_gbs": mb / (mms * 1e-3) / 1e9,
+                                           "frac": mb / (mms * 1e-3) / 1e9 / peak}
+    if e2e_steps:
+        # end to end through the public entry point with host buffers: H2D of the step's state from
+        # pinned memory, the step, D2H of its result, every step; each step's status is checked
+        ke = min(steps, e2e_steps)
+        host = {k: st[k].cpu().pin_memory() for k in ("u", "U", "p", "H")}
+        dev = {k: torch.empty_like(st[k]) for k in host}
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        stats = L.Stats()
+        torch.cuda.synchronize()
+        barrier(world)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for q in range(ke):
+            for k in host:
+                dev[k].copy_(host[k], non_blocking=True)
+            rc = solver.step_raw(dev["u"], dev["U"], dev["p"], dev["H"], False, stats=stats)
+            if rc != 0 or not (stats.relres <= tol):
+                raise RuntimeError("end-to-end step failed: rc %d, relres %.3e" % (rc, stats.relres))
+            for k in host:
+                host[k].copy_(dev[k], non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e2.elapsed_time(e3), world)
+        out["e2e"] = {"value": N * ke * world / (ms_e2e * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": h2d, "steps": ke}
+        del host, dev
+    out["_solver"], out["_state"], out["_geo"] = solver, st, geo
+    return out
+
+
+def release(m):
+    for k in ("_solver", "_state", "_geo"):
+        obj = m.pop(k, None)
+        if k == "_solver" and obj is not None:
+            obj.close()
+        del obj
+
+
+def train_guess(L, torch, args):
+    """Snapshots (b, p^n, p^{n-1}, p^{n+1}) of the solver's own steps on the dirty sphere, then Adam
+    steps on the GPU with the library's forward and backward kernels."""
+    cfg, g, geo, solver = make_solver(L, torch, TRAIN_WORKLOAD, args)
+    st = solver.fields(W.initial_fields(cfg))
+    for _ in range(args.learn_spinup):
+        checked_step(L, solver, st, cfg.tol)
+    N = cfg.ncell
     snaps = []
     p_prev = st["p"].clone()
     t0 = time.time()
-    for n in range(args.learn_snapshots + 2):
+    for n in range(args.learn_snapshots + 1):
         p_n = st["p"].clone()
-        solver.step(st)
+        checked_step(L, solver, st, cfg.tol)
         b = torch.empty(N, dtype=torch.float64, device="cuda")
         solver.last_rhs(b)
-        if n >= 2:
+        if n >= 1:
             snaps.append((b, p_n, p_prev, st["p"].clone()))
         p_prev = p_n
     torch.cuda.synchronize()
     t_collect = time.time() - t0
     net = L.Net(net_init())
-    t0 = time.time()
     losses = []
+    t0 = time.time()
     for epoch in range(args.learn_epochs):
         for (b, p_n, p_p, p_next) in snaps:
             _, sc = net.forward(g, b, p_n, p_p, geo.flags)
@@ -334,38 +563,99 @@ def run_learned(args, L, torch, solver, st, geo, cfg, world):
             losses.append(net.train_step(g, b, p_n, p_p, target, args.learn_lr, geo.flags))
     torch.cuda.synchronize()
     t_train = time.time() - t0
-    del snaps
+    solver.close()
+    del snaps, st, geo
     torch.cuda.empty_cache()
-    ms_plain, st_plain = timed_steps(torch, solver, st, args.steps, stream)
+    return net, {"workload": TRAIN_WORKLOAD, "snapshots": args.learn_snapshots, "epochs": args.learn_epochs,
+                 "lr": args.learn_lr, "loss_first": losses[0], "loss_last": losses[-1],
+                 "collect_s": t_collect, "train_s": t_train}
+
+
+def learned_vs_plain(L, torch, m, net, train, args, world, stream):
+    """K steps without and K steps with the guess, consecutive windows from the same solver state."""
+    solver, st = m["_solver"], m["_state"]
+    tol = solver.params.tol
+    N = m["cells"]
+    ms_plain, st_plain, _ = timed_steps(L, torch, solver, st, args.steps, tol, stream)
     solver.attach_guess(net)
-    solver.step(st)                       # the guess needs p^{n-1}
-    ms_learn, st_learn = timed_steps(torch, solver, st, args.steps, stream)
+    checked_step(L, solver, st, tol)                      # the guess needs p^{n-1}
+    ms_learn, st_learn, _ = timed_steps(L, torch, solver, st, args.steps, tol, stream)
     solver.attach_guess(None)
     ms_plain = max_over_ranks(ms_plain, world)
     ms_learn = max_over_ranks(ms_learn, world)
     ratios = [s["relres_guess"] / s["relres0"] for s in st_learn if s["relres0"] > 0]
-    net.close()
-    return {
-        "value": N * args.steps * world / (ms_learn * 1e-3) / 1e6,
-        "ms_per_step": ms_learn / args.steps,
-        "plain_same_window": {"value": N * args.steps * world / (ms_plain * 1e-3) / 1e6,
-                              "ms_per_step": ms_plain / args.steps,
-                              "inner_iters_per_step": float(np.mean([s["iters"] for s in st_plain])),
-                              "refinements_per_step": float(np.mean([s["outer"] for s in st_plain]))},
-        "inner_iters_per_step": float(np.mean([s["iters"] for s in st_learn])),
-        "refinements_per_step": float(np.mean([s["outer"] for s in st_learn])),
-        "guess_used_fraction": float(np.mean([s["guess_used"] for s in st_learn])),
-        "median_initial_residual_ratio": float(np.median(ratios)) if ratios else None,
-        "max_relres": float(max(s["relres"] for s in st_learn)),
-        "train": {"snapshots": args.learn_snapshots, "epochs": args.learn_epochs, "lr": args.learn_lr,
-                  "loss_first": losses[0], "loss_last": losses[-1], "collect_s": t_collect, "train_s": t_train},
-        "note": "plain and learned windows are consecutive, after the training snapshots; same solver state",
-    }
+    return {"workload": m["workload"], "value": N * args.steps * world / (ms_learn * 1e-3) / 1e6,
+            "ms_per_step": ms_learn / args.steps, "solve": solve_summary(st_learn),
+            "guess_used_fraction": float(np.mean([s["guess_used"] for s in st_learn])),
+            "median_initial_residual_ratio": float(np.median(ratios)) if ratios else None,
+            "plain_same_window": {"value": N * args.steps * world / (ms_plain * 1e-3) / 1e6,
+                                  "ms_per_step": ms_plain / args.steps, "solve": solve_summary(st_plain)},
+            "speedup": ms_plain / ms_learn, "train": train,
+            "note": "plain window first, then the learned window, from the same solver state; the network "
+                    "is trained on snapshots of a different workload (%s)" % TRAIN_WORKLOAD}
+
+
+def roofline_of(m, workload):
+    """Roofline object of the dominant single-kernel group of a measured workload."""
+    groups = {k: v for k, v in m["groups"].items() if k != "momentum_per_step"}
+    dom = max(groups, key=lambda k: groups[k]["launches"] * groups[k]["avg_launch_ms"])
+    g = groups[dom]
+    peak, kind = m["peak"]
+    names = dict(GROUP_KERNEL, **(GROUP_KERNEL_FUSED if m.get("mg", {}).get("fused_fine_passes") else {}))
+    return {"bound": "hbm", "kernel": dom, "kernel_name": names.get(dom, dom), "mg": m.get("mg"),
+            "achieved": g["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": g["achieved_gbs"] / peak,
+            "traffic": ncu_traffic(dom, workload), "algorithmic_bytes_per_launch": g["bytes_per_launch"],
+            "avg_launch_ms": g["avg_launch_ms"], "peak_source": kind, "shares": m["shares"],
+            "groups": m["groups"],
+            "note": "kernel times from a second pass of the same number of steps with per-kernel events on the "
+                    "launching stream (graphs off); frac is of the measured copy peak"}
+
+
+def cpu_baseline(args, iters, pool_result):
+    """Oracle timings on the host cores: one thread and all cores on slab steps of the headline workload
+    (each process its own slab), and the small workload run in full on one thread."""
+    import multiprocessing as mp
+    name = args.workload
+    cfg = W.get_config(name)
+    planes = 1 if cfg.ncell > 50_000_000 else 2
+    one = oracle_sample_step(name, iters, planes, integrator=args.integrator, quick=args.quick)
+    ncores = os.cpu_count() or 1
+    k0s = [int(v) for v in np.linspace(0, cfg.nz // 2 - planes, ncores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(ncores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_sample_worker, [(name, iters, planes, k, args.integrator, args.quick) for k in k0s])
+        wall = time.perf_counter() - t0
+    all_cells = sum(r["cells"] for r in res)
+    # the slab-steps' own compute time (processes start and classify before they time)
+    slowest = max(r["seconds"] for r in res)
+    full = pool_result.get() if pool_result is not None else None
+    out = {"value": one["cells"] / one["seconds"] / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": _sample_desc(name, planes, iters, args.integrator),
+           "host_cores": ncores,
+           "all_cores": {"value": all_cells / slowest / 1e6, "cores": ncores, "wall_s_incl_setup": wall,
+                         "note": "%d processes, each one slab step of the same workload at a different height, "
+                                 "timed concurrently; value = total slab cells / slowest process's step time"
+                                 % ncores}}
+    if full is not None:
+        cells, steps, secs = full
+        out["full_run"] = {"workload": FP64_SMALL, "cells": cells, "steps": steps, "seconds": secs,
+                           "value": cells * steps / secs / 1e6, "cores": 1,
+                           "note": "the whole 50-step FP64 workload to 1e-10 (oracle BiCGStab), one thread"}
+    return out
 
 
 def run_ours(args):
-    import torch
+    import multiprocessing as mp
     rank, world, local = dist_env()
+    # the oracle's full run of the small workload goes in a spawned process started before any GPU call,
+    # on one host core while the GPU is measured
+    full_pool = None
+    full_res = None
+    if rank == 0 and not args.no_cpu_baseline:
+        full_pool = mp.get_context("spawn").Pool(1)
+        full_res = full_pool.apply_async(_full_run_worker, (FP64_SMALL,))
+    import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -373,158 +663,74 @@ def run_ours(args):
     from paper_2002_06206_gb300 import build
     build.build()
     from paper_2002_06206_gb300 import ibmles as L
-
-    cfg = W.get_config(args.workload)
-    tri = cfg.soup()
-    g = L.make_grid(cfg.nx, cfg.ny, cfg.nz, cfg.dx)
-    geo = L.Geometry(g, torch.from_numpy(tri).cuda(), deadend_on=cfg.deadend_on)
-    precond = L.MULTIGRID if args.precond == "mg" else L.NO_PRECOND
-    integ = L.CRANK_NICOLSON if args.integrator == "cn" else L.ADAMS_BASHFORTH
-    solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=cfg.precision, solver=L.CG, tol=cfg.tol,
-                      max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
-                      csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo, precond=precond,
-                      quick=args.quick, integrator=integ, mg_sweeps=args.mg_sweeps,
-                      mg_omega=args.mg_omega)
-    st = solver.fields(W.initial_fields(cfg))
-    for _ in range(args.warmup):
-        solver.step(st)
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    props = torch.cuda.get_device_properties(local)
-    gpu_id = "GPU-" + str(props.uuid) if getattr(props, "uuid", None) else str(local)
 
-    # ---- timed region: K steps, inputs resident in HBM, the library's fast path (CUDA graphs on)
-    iters, outers, relres, moms = [], [], [], []
-    solver.profile(0)
-    n_launch0 = solver.kernel_launches()
-    barrier(world)
-    torch.cuda.synchronize()
-    with Clocks(gpu_id) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            s = solver.step(st)
-            iters.append(s.iters)
-            outers.append(s.outer)
-            relres.append(s.relres)
-            moms.append(s.mom_iters)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = solver.kernel_launches() - n_launch0
-    barrier(world)
-    ms_max = max_over_ranks(ms, world)
-    clocks = clk.summary()
+    # ---- headline: the largest workload, FP32 + FP64 refinement
+    head = measure(L, torch, args.workload, args, world, stream, profile=True, e2e_steps=args.e2e_steps, clocks=True)
+    roof = roofline_of(head, args.workload)
+    release(head)
+    torch.cuda.empty_cache()
+    classify = None if args.no_classify else time_classify(L, torch, args.workload)
 
-    # ---- the same number of steps again with per-kernel CUDA events on the launching stream (the
-    # profiler records around every kernel group, so graphs are not used here): kernel durations
-    solver.profile(1)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        solver.step(st)
-    torch.cuda.synchronize()
-    prof = solver.profile_read()
-    solver.profile(0)
+    # ---- the cube-and-plate workload: plain, then learned vs plain in the same window
+    second = None
+    if not args.no_secondary:
+        net, train = (None, None)
+        if not args.no_learned:
+            net, train = train_guess(L, torch, args)
+        sm = measure(L, torch, SECONDARY, args, world, stream, steps=args.steps, warmup=args.warmup, profile=True)
+        second = {k: sm[k] for k in ("workload", "cells", "value", "ms_per_step", "steps", "timed_steps", "solve")}
+        second["roofline"] = {k: v for k, v in roofline_of(sm, SECONDARY).items() if k not in ("shares",)}
+        if net is not None:
+            second["learned"] = learned_vs_plain(L, torch, sm, net, train, args, world, stream)
+            net.close()
+        release(sm)
+        torch.cuda.empty_cache()
 
-    # ---- end to end through the public API with host buffers: H2D of the step's inputs from pinned
-    # memory, the step, D2H of its result, every step
-    ke = min(args.steps, args.e2e_steps)
-    host = {k: st[k].cpu().pin_memory() for k in ("u", "U", "p", "H")}
-    dev = {k: torch.empty_like(st[k]) for k in host}
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
-    d2h = h2d
-    torch.cuda.synchronize()
-    barrier(world)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    n0 = st["n"]
-    for q in range(ke):
-        for k in host:
-            dev[k].copy_(host[k], non_blocking=True)
-        solver.step_raw(dev["u"], dev["U"], dev["p"], dev["H"], False)
-        for k in host:
-            host[k].copy_(dev[k], non_blocking=True)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e2.elapsed_time(e3), world)
-    del n0
-
-    N = cfg.ncell
-    value = N * args.steps * world / (ms_max * 1e-3) / 1e6
-    e2e_value = N * ke * world / (ms_e2e * 1e-3) / 1e6
-
-    # ---- roofline of the dominant kernel group
-    s_bytes = 8 if cfg.precision == L.FP64 else 4
-    bpc = bytes_per_cell(s_bytes, args.integrator)
-    timed = {k: v for k, v in prof.items() if v[1] > 0 and k in bpc}
-    everything = {k: v for k, v in prof.items() if v[1] > 0}
-    M = float(np.mean(moms))
-    peak, peak_kind = read_peaks()
-    # every group with a byte model: achieved = algorithmic bytes per launch / mean launch time
-    groups = {}
-    for k, (ms_k, n_k) in timed.items():
-        gbs = bpc[k] * N / (ms_k / n_k * 1e-3) / 1e9
-        groups[k] = {"launches": n_k, "avg_launch_ms": ms_k / n_k, "bytes_per_launch": bpc[k] * N,
-                     "achieved_gbs": gbs, "frac": gbs / peak}
-    if args.integrator == "cn" and prof["momentum"][1] > 0:
-        # the momentum BiCGStab per step (several kernel kinds): M iterations of p update (r, p, v ->
-        # p), two operator passes (input, U, nu_t, flags -> output, one dot operand), s update
-        # (r, v -> s), x/r update (x, p, s, t, r_hat -> x, r): (68 s + 2) bytes per cell per iteration
-        mb = M * (68 * s_bytes + 2) * N
-        mms = prof["momentum"][0] / args.steps
-        groups["momentum_per_step"] = {"launches": args.steps, "avg_launch_ms": mms, "bytes_per_launch": mb,
-                                       "achieved_gbs": mb / (mms * 1e-3) / 1e9,
-                                       "frac": mb / (mms * 1e-3) / 1e9 / peak}
-    # the dominant single kernel (one kernel kind per launch of the group)
-    dom = max(timed, key=lambda k: timed[k][0])
-    avg_ms = timed[dom][0] / timed[dom][1]
-    algo_bytes = bpc[dom] * N
-    achieved = algo_bytes / (avg_ms * 1e-3) / 1e9
-    shares = {k: round(v[0] / sum(x[0] for x in everything.values()), 4) for k, v in everything.items()}
-
-    learned = run_learned(args, L, torch, solver, st, geo, cfg, world) if args.learned else None
-    classify = None if args.no_classify else time_classify(L, torch)
+    # ---- the pure-FP64 path
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = {}
+        small = W.get_config(FP64_SMALL)
+        f1 = measure(L, torch, FP64_SMALL, args, world, stream, precision=L.FP64, steps=small.steps, warmup=0,
+                     profile=False, own_scheme=True)
+        fp64[FP64_SMALL] = {k: f1[k] for k in ("cells", "value", "ms_per_step", "steps", "solve")}
+        fp64[FP64_SMALL]["note"] = ("the whole 50-step workload from its initial field with its own scheme (AB2, "
+                                    "central advection), tol 1e-10; L2-resident, as the oracle's full run")
+        release(f1)
+        f3 = measure(L, torch, SECONDARY, args, world, stream, precision=L.FP64, steps=max(args.steps // 2, 5),
+                     warmup=args.warmup, profile=True)
+        fp64[SECONDARY] = {k: f3[k] for k in ("cells", "value", "ms_per_step", "steps", "solve")}
+        fp64[SECONDARY]["roofline"] = {k: v for k, v in roofline_of(f3, SECONDARY).items() if k not in ("shares",)}
+        release(f3)
+        torch.cuda.empty_cache()
 
     line = None
     if rank == 0:
-        I = float(np.mean(iters))
-        cpu = oracle_sample(cfg, I, integrator=args.integrator, quick=args.quick) if not args.no_cpu_baseline else None
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(args, int(round(head["solve"]["inner_iters_per_step"])), full_res)
+            full_pool.close()
+            full_pool.join()
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": N, "grid": [cfg.nx, cfg.ny, cfg.nz],
-                       "triangles": int(len(tri)), "precision": "fp32 stencils and cg, fp64 residual refinement",
-                       "solver": "cg + multigrid V-cycle" if precond else "cg", "tol": cfg.tol,
-                       "integrator": "crank-nicolson" if args.integrator == "cn" else "adams-bashforth-2",
-                       "quick": args.quick, "mg_sweeps": args.mg_sweeps if precond else None,
-                       "mg_omega": args.mg_omega if precond else None,
-                       "momentum_bicgstab_iters_per_step": M,
-                       "timed_steps": [args.warmup + 1, args.warmup + args.steps],
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (~0.4 GB of state per step vs 126 MB L2)",
-                       "inner_iters_per_step": I, "refinements_per_step": float(np.mean(outers)),
-                       "max_relres": float(np.max(relres))},
-            "roofline": {"bound": "hbm", "kernel": dom, "kernel_name": GROUP_KERNEL.get(dom, dom),
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": ncu_traffic(dom),
-                         "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ms,
-                         "peak_source": peak_kind, "shares": shares, "groups": groups,
-                         "note": "kernel times from a second pass of the same number of steps with per-kernel "
-                                 "events (graphs off); shares are of event-timed kernel time"},
-            "cpu_baseline": None if cpu is None else {
-                "value": N / cpu["t_step_s"] / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": cpu["sample"]},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": ke},
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "config": dict(workload_config(args.workload, args), parallelism="replicas" if world > 1 else "single"),
+            "solve": head["solve"], "timed_steps": head["timed_steps"],
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": head.get("e2e"),
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
             "classify": classify,
-            "learned": learned,
+            "secondary": second,
+            "learned": second.get("learned") if second else None,
+            "fp64": fp64,
         }
         print(json.dumps(line), flush=True)
+    elif full_pool is not None:
+        full_pool.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -534,8 +740,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=30)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--check-every", type=int, default=8)
@@ -549,7 +755,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-classify", action="store_true")
-    ap.add_argument("--learned", action="store_true", help="also time the learned initial guess")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the cube-and-plate line (and the learned guess)")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--learn-spinup", type=int, default=30)
     ap.add_argument("--learn-snapshots", type=int, default=24)
     ap.add_argument("--learn-epochs", type=int, default=8)
     ap.add_argument("--learn-lr", type=float, default=2e-3)

@@ -80,6 +80,11 @@ typedef struct {
     int32_t mom_max_iter;/* Crank-Nicolson: BiCGStab iteration cap per step (0 = 200) */
     double mom_tol;      /* Crank-Nicolson: stop at ||r|| <= mom_tol ||dt L(u^n)|| (0 = 1e-6 in
                             FP32_REFINE64 mode, 1e-10 in FP64 mode) */
+    int32_t mg_passes;   /* multigrid fine-grid passes: 0 = fused where the grid allows (FP32, mg_sweeps 2,
+                            nx a multiple of 16, no periodic axis, a body present: the four half-sweeps
+                            before the coarse correction and the restriction in one pass, the four after
+                            it and (r, z) in another), 1 = one kernel per half-sweep.  Same V-cycle. */
+    int32_t reserved;
 } les_params;
 
 typedef struct {
@@ -215,6 +220,17 @@ int poisson_apply(les_state* st, const double* d_p, double* d_Ap, void* stream);
 int poisson_solve(les_state* st, const double* d_b, double* d_p, double tol, int32_t max_it,
                   int32_t solver, les_stats* stats, void* stream);
 
+/* The multigrid preconditioner of the pressure solve (not in the paper, whose solvers are BiCGStab and
+ * red-black SOR): d_z[N] = one V-cycle applied to d_r[N], in the state's working precision (float in
+ * FP32_REFINE64 mode, double in FP64 mode), for the unscaled system  sum_links g (z_N - z_P) - d z_P =
+ * dx^2 r  whose operator is dx^2 times the Eq. poisson operator.  Both arrays are 16-byte aligned and
+ * distinct.  Needs a state created with precond = 1.  Synchronises (reads a device error word). */
+int poisson_precond(les_state* st, const void* d_r, void* d_z, void* stream);
+/* Multigrid hierarchy of a state (host, no synchronisation): out[0] = levels (0 without multigrid),
+ * out[1] = 1 when the fused fine-grid passes are used, out[2 + l] = unknowns of level l (level 0 =
+ * cells), for the first n - 2 levels.  n >= 2. */
+int les_mg_info(const les_state* st, int64_t* out, int32_t n);
+
 /* Forces on the body (Sec. 3.2-3.3), out (host) = 12 doubles; synchronises.
  *  out[0..2]  Eq. force: Shepard inverse-distance pressure on the front/back of every triangle,
  *             F = sum_tri area (p_back - p_front) n;  out[3] = triangles used (both sides found);
@@ -292,6 +308,12 @@ int ibm_net_train_step(ibm_net* net, const ibm_grid* grid, const double* d_b, co
 int les_attach_guess(les_state* st, ibm_net* net);
 /* Copy the right-hand side b of the last les_step / les_rhs into d_b[N]. */
 int les_last_rhs(les_state* st, double* d_b, void* stream);
+
+/* Measured fused multiply-add rate of the current GPU in TFLOP/s (2 flops per FMA), FP64
+ * (precision = IBM_FP64) or FP32 (IBM_FP32_REFINE64): independent FMA chains on every SM, best of three
+ * launches timed with CUDA events on `stream`.  Not in the paper: the arithmetic roof beside the HBM
+ * roof in performance reports.  Allocates 16 bytes (stream-ordered); synchronises. */
+int ibm_probe_fma_rate(int32_t precision, double* tflops, void* stream);
 
 /* Number of faces NF of the concatenated face vector for this grid (-1 for an invalid grid). */
 int64_t les_num_faces(const ibm_grid* grid);

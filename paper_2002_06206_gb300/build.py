@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibmles.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = {"classify.cu": ["-fmad=false"], "surface.cu": ["-fmad=false"], "les.cu": [], "poisson.cu": [], "mg.cu": [],
-           "stencil4.cu": [], "learn.cu": [], "api.cu": []}
+           "stencil4.cu": [], "learn.cu": [], "api.cu": [], "probe.cu": []}
 
 
 def nvcc():

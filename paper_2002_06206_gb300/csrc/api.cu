@@ -159,6 +159,7 @@ static int check_params(const les_params* p) {
     if (p->precond && p->mg_omega != 0.0 && !(p->mg_omega > 0.0 && p->mg_omega < 2.0))
         return ibm_fail(IBM_E_INVALID, "mg_omega must lie in (0, 2) for a symmetric positive preconditioner");
     if (p->precond && p->mg_sweeps < 0) return ibm_fail(IBM_E_INVALID, "mg_sweeps must be >= 0");
+    if (p->mg_passes != 0 && p->mg_passes != 1) return ibm_fail(IBM_E_INVALID, "mg_passes must be 0 or 1");
     if (!(p->quick >= 0.0 && p->quick <= 1.0)) return ibm_fail(IBM_E_INVALID, "quick must lie in [0, 1]");
     if (p->integrator != IBM_ADAMS_BASHFORTH && p->integrator != IBM_CRANK_NICOLSON)
         return ibm_fail(IBM_E_INVALID, "unknown integrator %d", p->integrator);
@@ -296,7 +297,10 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
         }
     }
     if (p->precond == 1) {
-        MG* mg = (MG*)calloc(1, sizeof(MG));
+        // MG holds 64-byte aligned tensor maps
+        const size_t mgb = (sizeof(MG) + 63) & ~(size_t)63;
+        MG* mg = (MG*)aligned_alloc(64, mgb);
+        if (mg) memset(mg, 0, mgb);
         if (!mg) {
             free_state(S);
             return ibm_fail(IBM_E_NOMEM, "les_create: host allocation");
@@ -305,6 +309,7 @@ extern "C" int les_create(const ibm_grid* g, const les_params* p, const ibm_geom
         mg->sweeps = p->mg_sweeps > 0 ? p->mg_sweeps : 2;
         mg->omega = p->mg_omega > 0.0 ? p->mg_omega : 1.6;
         mg->coarse_sweeps = 8;
+        mg->allow_fused = p->mg_passes == 0;
         ALLOC(S->w.z, N * s);
         if ((e = cudaStreamCreateWithFlags(&S->w.cap, cudaStreamNonBlocking)) != cudaSuccess) {
             free_state(S);
@@ -474,6 +479,35 @@ extern "C" int poisson_solve(les_state* S, const double* b, double* p, double to
     if (rc == IBM_E_NOCONV) ibm_fail(rc, "poisson_solve: no convergence within %d iterations", max_it);
     if (rc == IBM_E_NONFINITE) ibm_fail(rc, "poisson_solve: residual is not finite");
     return rc;
+}
+
+extern "C" int poisson_precond(les_state* S, const void* r, void* z, void* stream) {
+    NEED(S); NEED(r); NEED(z);
+    if (!S->c.mg) return ibm_fail(IBM_E_INVALID, "poisson_precond: the state has no multigrid preconditioner");
+    if ((((uintptr_t)r) | ((uintptr_t)z)) & 15u)
+        return ibm_fail(IBM_E_INVALID, "poisson_precond: r and z must be 16-byte aligned");
+    if (r == z) return ibm_fail(IBM_E_INVALID, "poisson_precond: r and z must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_reset(S->w.sc, s);
+    int rc = S->c.prec == IBM_FP64 ? mg_vcycle<double>(S->c, *S->c.mg, (const double*)r, (double*)z, S->w.sc, s)
+                                  : mg_vcycle<float>(S->c, *S->c.mg, (const float*)r, (float*)z, S->w.sc, s);
+    if (rc) return rc;
+    IBM_CUDA(cudaMemcpyAsync(S->w.hsc, S->w.sc, sizeof(SolveScal), cudaMemcpyDeviceToHost, s));
+    IBM_CUDA(cudaStreamSynchronize(s));
+    if (S->w.hsc->dev_error) return ibm_fail(IBM_E_CUDA, "poisson_precond: a multigrid shared-memory load timed out");
+    return IBM_OK;
+}
+
+extern "C" int les_mg_info(const les_state* S, int64_t* out, int32_t n) {
+    NEED(S); NEED(out);
+    if (n < 2) return ibm_fail(IBM_E_INVALID, "les_mg_info: n must be >= 2");
+    for (int q = 0; q < n; ++q) out[q] = 0;
+    if (!S->c.mg) return IBM_OK;
+    const MG& mg = *S->c.mg;
+    out[0] = mg.nlev;
+    out[1] = mg.fused;
+    for (int l = 0; l < mg.nlev && 2 + l < n; ++l) out[2 + l] = mg.lev[l].M;
+    return IBM_OK;
 }
 
 extern "C" int les_step(les_state* S, void* u, void* U, double* p, void* H, int32_t first, les_stats* st,

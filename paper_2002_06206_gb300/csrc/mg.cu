@@ -19,7 +19,10 @@
 //
 // Equations are solved in the unscaled form  sum_links g (x_N - x_P) - d x_P = dx^2 r.
 #include <cooperative_groups.h>
+#include <cudaTypedefs.h>
 #include <string.h>
+
+#include <mutex>
 #include <type_traits>
 
 #include "scan.cuh"
@@ -223,6 +226,416 @@ __device__ __forceinline__ int fine_parts(const Dom& D, const unsigned (&fl)[8],
     for (int m = 0; m < 8; ++m) part[m] = __popc(roots & ((1u << lab[m]) - 1u));
     return __popc(roots);
 }
+
+// ---- fused fine-grid passes: all four red-black half-sweeps of a smoothing phase in one pass ------
+//
+// A block owns an (x, y) tile of FT_TX x FT_TY cells and marches along z over a chunk of planes.  It
+// keeps, for the tile plus a 4-cell halo, a ring of FT_NS planes of r, flags and z in shared memory;
+// the planes arrive by TMA (one elected thread issues cp.async.bulk.tensor loads one plane ahead; an
+// mbarrier per ring slot carries the byte count).  Step t takes plane t; the half-sweeps run at planes
+// t, t-1, t-2, t-3 (each needs its neighbours after the previous half-sweep, one plane and one halo
+// cell further out), so that after step t plane t-3 (pre-smoothing) or t-4 (post-smoothing) is final.
+// The halo shrinks by one cell per half-sweep, so the tile's own cells see exactly the values the
+// four separate passes compute.  Pre-smoothing starts from z = 0 (only r and the flags are read) and
+// ends with the residual and its restriction to level 1; post-smoothing reads z and ends with the
+// (r, z) product of the CG iteration.  Neighbouring chunks recompute each other's edge planes but
+// only write their own.
+
+#define FT_TX 48                    // tile along x (a multiple of 16: the flags box starts 16 cells left)
+#define FT_TY 20                    // tile along y (even: level-1 blocks are 2 x 2 x 2)
+#define FT_H 4                      // halo
+#define FT_RX (FT_TX + 2 * FT_H)    // r / z box along x (56 floats = 224 bytes)
+#define FT_RY (FT_TY + 2 * FT_H)    // box along y
+#define FT_FX (FT_TX + 32)          // flags box along x (80 bytes), starting 16 cells left of the tile
+#define FT_FOFF 12                  // flags column of r/z column 0
+#define FT_NS 7                     // ring slots: planes t-5 .. t+1
+#define FT_NT 512                   // threads
+#define FT_RBYTES (FT_RX * FT_RY * 4)
+#define FT_FBYTES (FT_FX * FT_RY)
+#define FT_FPAD (((FT_FBYTES + 127) / 128) * 128)
+#define FT_SLOT (2 * FT_RBYTES + FT_FPAD)             // r | z | flags
+#define FT_SMEM (FT_NS * FT_SLOT + 2 * FT_TX * FT_TY * 4 + 8 * FT_NS + 128)   // + alignment slack
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity, for at most about a second (clock cycles); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 2000000000LL) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+struct FTSmem {
+    unsigned char* base;
+    __device__ float* r(int s) const { return reinterpret_cast<float*>(base + s * FT_SLOT); }
+    __device__ float* z(int s) const { return reinterpret_cast<float*>(base + s * FT_SLOT + FT_RBYTES); }
+    __device__ const uint8_t* f(int s) const { return base + s * FT_SLOT + 2 * FT_RBYTES; }
+    __device__ float* res(int parity) const { return reinterpret_cast<float*>(base + FT_NS * FT_SLOT) + parity * FT_TX * FT_TY; }
+    __device__ uint64_t* bar(int s) const {
+        return reinterpret_cast<uint64_t*>(base + FT_NS * FT_SLOT + 2 * FT_TX * FT_TY * 4) + s;
+    }
+};
+
+struct FTPos {
+    int x0, y0, gx0, gy0;   // tile origin; global coordinates of ring column / row 0
+    int tlo;                // first plane loaded (ring slot 0, use 0)
+};
+
+__device__ __forceinline__ int ft_slot(const FTPos& P, int t) { return (t - P.tlo) % FT_NS; }
+__device__ __forceinline__ unsigned ft_parity(const FTPos& P, int t) { return (unsigned)(((t - P.tlo) / FT_NS) & 1); }
+
+// Issues the TMA loads of plane t (r and flags, and z when `withz`) into its slot, or, for a plane
+// outside the domain, just completes the slot's phase.  One thread.
+__device__ __forceinline__ void ft_issue(const Dom& D, const FTSmem& S, const FTPos& P, int t, bool withz,
+                                         const CUtensorMap* tr, const CUtensorMap* tz, const CUtensorMap* tf) {
+    const int s = ft_slot(P, t);
+    uint64_t* b = S.bar(s);
+    if (t < 0 || t >= D.nz) {
+        mbar_arrive(b);
+        return;
+    }
+    mbar_expect_tx(b, (withz ? 2 : 1) * FT_RBYTES + FT_FBYTES);
+    tma_load3(S.r(s), tr, P.gx0, P.gy0, t, b);
+    if (withz) tma_load3(S.z(s), tz, P.gx0, P.gy0, t, b);
+    tma_load3((void*)S.f(s), tf, P.gx0 - FT_FOFF, P.gy0, t, b);
+}
+
+// Gauss-Seidel value of ring cell (rx, ry) of plane t:  (sum of z over the open links - scale r) / dg,
+// dg = open links + the outflow terms.  The interior case (no cut link, not on a domain face) sums the
+// six neighbours as the separate passes do.
+__device__ __forceinline__ float ft_gs(const Dom& D, const FTSmem& S, const FTPos& P, int t, int rx, int ry,
+                                       float scale, const float* zm, const float* zc, const float* zp,
+                                       const float* rc, const uint8_t* fc) {
+    const int c = ry * FT_RX + rx;
+    const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
+    const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+    const float sr = scale * rc[c];
+    if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1) {
+        const float s = ((zc[c - 1] + zc[c + 1]) + (zc[c - FT_RX] + zc[c + FT_RX])) + (zm[c] + zp[c]);
+        return (s - sr) * (1.f / 6.f);
+    }
+    const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
+    float s = 0.f, dg = 0.f;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        const int a = b >> 1, sd = (b & 1) ? 1 : -1;
+        const bool in = g[a] + sd >= 0 && g[a] + sd < n[a];
+        if (in && !(fl & (1u << b))) {
+            dg += 1.f;
+            s += a == 0 ? zc[c + sd] : (a == 1 ? zc[c + sd * FT_RX] : (sd < 0 ? zm[c] : zp[c]));
+        } else if (!in && D.bc[b] == IBM_BC_OUTFLOW) {
+            dg += 2.f;
+        }
+    }
+    return dg == 0.f ? 0.f : (s - sr) / dg;
+}
+
+// A * z at ring cell (rx, ry) of plane t in the unscaled form  sum_open (z_N - z_P) - d z_P.
+__device__ __forceinline__ float ft_az(const Dom& D, const FTPos& P, int t, int rx, int ry, const float* zm,
+                                       const float* zc, const float* zp, const uint8_t* fc) {
+    const int c = ry * FT_RX + rx;
+    const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
+    const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+    const float zP = zc[c];
+    if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1)
+        return ((zc[c - 1] + zc[c + 1]) + (zc[c - FT_RX] + zc[c + FT_RX])) + (zm[c] + zp[c]) - 6.f * zP;
+    const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
+    float s = 0.f;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        const int a = b >> 1, sd = (b & 1) ? 1 : -1;
+        const bool in = g[a] + sd >= 0 && g[a] + sd < n[a];
+        if (in && !(fl & (1u << b)))
+            s += (a == 0 ? zc[c + sd] : (a == 1 ? zc[c + sd * FT_RX] : (sd < 0 ? zm[c] : zp[c]))) - zP;
+        else if (!in && D.bc[b] == IBM_BC_OUTFLOW)
+            s += -zP - zP;
+    }
+    return s;
+}
+
+// One half-sweep of colour `col` on plane t over the ring cells within `e` of the tile.  A half-sweep
+// of the k-th kind (k = 1, 2, 3) runs only on planes t >= tlo + k: below that its inputs (the previous
+// half-sweep on plane t - 1) were never formed in this block, and nothing it would produce is needed.
+__device__ __forceinline__ void ft_half_sweep(const Dom& D, const FTSmem& S, const FTPos& P, int t, int col, int e,
+                                              float scale, int kind) {
+    if (t < P.tlo + kind || t < 0 || t >= D.nz) return;
+    const int s = ft_slot(P, t);
+    float* zc = S.z(s);
+    const float* zm = S.z(ft_slot(P, t - 1));     // planes outside the domain are never read (links closed)
+    const float* zp = S.z(ft_slot(P, t + 1));
+    const float* rc = S.r(s);
+    const uint8_t* fc = S.f(s);
+    const int rlo = FT_H - e, rhi = FT_H + FT_TY + e;
+    const int clo = FT_H - e, chi = FT_H + FT_TX + e;
+    const int npr = FT_RX / 2;                      // cell pairs per ring row
+    const int n = npr * (rhi - rlo);
+    for (int q = threadIdx.x; q < n; q += FT_NT) {
+        const int ry = rlo + q / npr, pr = q % npr;
+        const int rx = 2 * pr + ((P.gx0 + P.gy0 + ry + t + col) & 1);
+        const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+        if (rx < clo || rx >= chi || gx < 0 || gx >= D.nx || gy < 0 || gy >= D.ny) continue;
+        zc[ry * FT_RX + rx] = ft_gs(D, S, P, t, rx, ry, scale, zm, zc, zp, rc, fc);
+    }
+}
+
+// Pre-smoothing (from z = 0, colours 0, 1, 0, 1) + restriction of  scale r - A z  to the parts of the
+// level-1 blocks.  Writes z on its chunk's planes [k0, k1) and b_1.
+__global__ void __launch_bounds__(FT_NT, 2) k_mg_pre_fused(Dom D, float* __restrict__ z, float scale, MGLev C1,
+                                                          int kchunk, SolveScal* sc,
+                                                          const __grid_constant__ CUtensorMap tmr,
+                                                          const __grid_constant__ CUtensorMap tmf) {
+    if (sc->done) return;
+    extern __shared__ __align__(128) unsigned char ft_smem[];
+    __shared__ int abort_flag;
+    FTSmem S{reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ft_smem) + 127) & ~(uintptr_t)127)};
+    FTPos P;
+    P.x0 = blockIdx.x * FT_TX;
+    P.y0 = blockIdx.y * FT_TY;
+    P.gx0 = P.x0 - FT_H;
+    P.gy0 = P.y0 - FT_H;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    P.tlo = k0 - 4;
+    const int thi = k1 + 3;
+    float* __restrict__ b1 = (float*)C1.b;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < FT_NS; ++s) mbar_init(S.bar(s), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ft_issue(D, S, P, P.tlo, false, &tmr, nullptr, &tmf);
+    int issued = P.tlo;
+    for (int t = P.tlo; t <= thi; ++t) {
+        if (threadIdx.x == 0 && t + 1 <= thi) {
+            ft_issue(D, S, P, t + 1, false, &tmr, nullptr, &tmf);
+            issued = t + 1;
+        }
+        if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        // h1 on plane t: z = -scale r / dg on colour 0, 0 on colour 1 (z = 0 before the first pass)
+        if (t >= 0 && t < D.nz) {
+            const int s = ft_slot(P, t);
+            float* zc = S.z(s);
+            const float* rc = S.r(s);
+            const uint8_t* fc = S.f(s);
+            for (int c = threadIdx.x; c < FT_RX * FT_RY; c += FT_NT) {
+                const int ry = c / FT_RX, rx = c % FT_RX;
+                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+                zc[c] = 0.f;
+                if (gx < 0 || gx >= D.nx || gy < 0 || gy >= D.ny || ((gx + gy + t) & 1)) continue;
+                const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
+                float dg = 0.f;
+                if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1) {
+                    zc[c] = (0.f - scale * rc[c]) * (1.f / 6.f);
+                    continue;
+                }
+                const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
+#pragma unroll
+                for (int b = 0; b < 6; ++b) {
+                    const int a = b >> 1, sd = (b & 1) ? 1 : -1;
+                    const bool in = g[a] + sd >= 0 && g[a] + sd < n[a];
+                    if (in && !(fl & (1u << b))) dg += 1.f;
+                    else if (!in && D.bc[b] == IBM_BC_OUTFLOW) dg += 2.f;
+                }
+                zc[c] = dg == 0.f ? 0.f : (0.f - scale * rc[c]) / dg;
+            }
+        }
+        __syncthreads();
+        ft_half_sweep(D, S, P, t - 1, 1, 3, scale, 1);
+        __syncthreads();
+        ft_half_sweep(D, S, P, t - 2, 0, 2, scale, 2);
+        __syncthreads();
+        ft_half_sweep(D, S, P, t - 3, 1, 1, scale, 3);
+        __syncthreads();
+        // plane t-3 is final: store the tile; residual of plane t-4 (its neighbours are final)
+        const int tw = t - 3, tr = t - 4;
+        if (tw >= k0 && tw < k1) {
+            const float* zc = S.z(ft_slot(P, tw));
+            for (int q = threadIdx.x; q < FT_TY * (FT_TX / 4); q += FT_NT) {
+                const int ry = FT_H + q / (FT_TX / 4), rx = FT_H + 4 * (q % (FT_TX / 4));
+                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+                if (gx >= D.nx || gy >= D.ny) continue;
+                const float* src = zc + ry * FT_RX + rx;
+                *reinterpret_cast<float4*>(z + gx + (long long)D.sy * gy + D.sz * tw) =
+                    make_float4(src[0], src[1], src[2], src[3]);
+            }
+        }
+        if (tr >= k0 && tr < k1) {
+            const int s = ft_slot(P, tr);
+            const float* zc = S.z(s);
+            const float* zm = S.z(ft_slot(P, tr - 1));
+            const float* zp = S.z(ft_slot(P, tr + 1));
+            const float* rc = S.r(s);
+            const uint8_t* fc = S.f(s);
+            float* res = S.res(tr & 1);
+            for (int q = threadIdx.x; q < FT_TX * FT_TY; q += FT_NT) {
+                const int ry = FT_H + q / FT_TX, rx = FT_H + q % FT_TX;
+                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+                float v = 0.f;
+                if (gx < D.nx && gy < D.ny) v = scale * rc[ry * FT_RX + rx] - ft_az(D, P, tr, rx, ry, zm, zc, zp, fc);
+                res[q] = v;
+            }
+            if ((tr & 1) || tr == D.nz - 1) {
+                __syncthreads();
+                // restriction: the level-1 blocks of planes (tr & ~1, tr | 1)
+                const int ke = tr & ~1;
+                const int Z = ke >> 1;
+                const unsigned both = (ke + 1 < D.nz) ? 1u : 0u;
+                const uint8_t* fe = S.f(ft_slot(P, ke));
+                const uint8_t* fo = S.f(ft_slot(P, ke + 1 < D.nz ? ke + 1 : ke));
+                for (int q = threadIdx.x; q < (FT_TX / 2) * (FT_TY / 2); q += FT_NT) {
+                    const int bx = q % (FT_TX / 2), by = q / (FT_TX / 2);
+                    const int X = (P.x0 >> 1) + bx, Y = (P.y0 >> 1) + by;
+                    if (X >= C1.px || Y >= C1.py) continue;
+                    unsigned fl[8];
+                    float rv[8];
+                    unsigned in = 0;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int di = m & 1, dj = (m >> 1) & 1, dk = m >> 2;
+                        const int gx = 2 * X + di, gy = 2 * Y + dj;
+                        const bool ok = gx < D.nx && gy < D.ny && (dk == 0 || both);
+                        const int rx = FT_H + 2 * bx + di, ry = FT_H + 2 * by + dj;
+                        fl[m] = ok ? (unsigned)(dk ? fo : fe)[ry * FT_FX + rx + FT_FOFF] : 0u;
+                        rv[m] = ok ? S.res(dk)[(2 * by + dj) * FT_TX + 2 * bx + di] : 0.f;
+                        in |= (ok ? 1u : 0u) << m;
+                    }
+                    int part[8];
+                    const int np = fine_parts(D, fl, in, part);
+                    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+#pragma unroll
+                        for (int s2 = 0; s2 < 8; ++s2) acc[s2] += part[m] == s2 ? rv[m] : 0.f;
+                    const int o = C1.off[X + (long long)C1.px * (Y + (long long)C1.py * Z)];
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; ++s2)
+                        if (s2 < np) b1[o + s2] = acc[s2];
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+    }
+    if (abort_flag && threadIdx.x == 0) {
+        // let the loads already issued land before the block's shared memory goes away
+        for (int u = issued; u > issued - FT_NS && u >= P.tlo; --u) mbar_wait(S.bar(ft_slot(P, u)), ft_parity(P, u));
+        atomicExch(&sc->dev_error, 1);
+    }
+}
+
+// Post-smoothing (colours 1, 0, 1, 0) of the iterate the coarse correction left (read through the
+// `tmz` map from an array this pass does not write), into z; then (r, z) over the grid:
+// rz_old = rz, rz = (r, z).
+__global__ void __launch_bounds__(FT_NT, 2) k_mg_post_fused(Dom D, float* __restrict__ z, float scale, int kchunk,
+                                                           SolveScal* sc, double* partials, unsigned* counter,
+                                                           const __grid_constant__ CUtensorMap tmr,
+                                                           const __grid_constant__ CUtensorMap tmz,
+                                                           const __grid_constant__ CUtensorMap tmf) {
+    if (sc->done) return;
+    extern __shared__ __align__(128) unsigned char ft_smem[];
+    __shared__ int abort_flag;
+    FTSmem S{reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(ft_smem) + 127) & ~(uintptr_t)127)};
+    FTPos P;
+    P.x0 = blockIdx.x * FT_TX;
+    P.y0 = blockIdx.y * FT_TY;
+    P.gx0 = P.x0 - FT_H;
+    P.gy0 = P.y0 - FT_H;
+    const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
+    P.tlo = k0 - 4;
+    const int thi = k1 + 3;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < FT_NS; ++s) mbar_init(S.bar(s), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ft_issue(D, S, P, P.tlo, true, &tmr, &tmz, &tmf);
+    int issued = P.tlo;
+    float part = 0.f;
+    for (int t = P.tlo; t <= thi; ++t) {
+        if (threadIdx.x == 0 && t + 1 <= thi) {
+            ft_issue(D, S, P, t + 1, true, &tmr, &tmz, &tmf);
+            issued = t + 1;
+        }
+        if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        ft_half_sweep(D, S, P, t - 1, 1, 3, scale, 1);
+        __syncthreads();
+        ft_half_sweep(D, S, P, t - 2, 0, 2, scale, 2);
+        __syncthreads();
+        ft_half_sweep(D, S, P, t - 3, 1, 1, scale, 3);
+        __syncthreads();
+        // last half-sweep on plane t-4 (colour 0, the tile only); each thread then stores its pair
+        // of cells and adds r z of both to the product
+        const int tf = t - 4;
+        if (tf >= k0 && tf < k1) {
+            const int s = ft_slot(P, tf);
+            float* zc = S.z(s);
+            const float* zm = S.z(ft_slot(P, tf - 1));
+            const float* zp = S.z(ft_slot(P, tf + 1));
+            const float* rc = S.r(s);
+            const uint8_t* fc = S.f(s);
+            for (int q = threadIdx.x; q < FT_TY * (FT_TX / 2); q += FT_NT) {
+                const int ry = FT_H + q / (FT_TX / 2), rx = FT_H + 2 * (q % (FT_TX / 2));
+                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+                if (gx >= D.nx || gy >= D.ny) continue;
+                const int m = (gx + gy + tf) & 1;          // the colour-0 cell of the pair is rx + m
+                const int c = ry * FT_RX + rx;
+                zc[c + m] = ft_gs(D, S, P, tf, rx + m, ry, scale, zm, zc, zp, rc, fc);
+                const float a = zc[c], b = zc[c + 1];
+                *reinterpret_cast<float2*>(z + gx + (long long)D.sy * gy + D.sz * tf) = make_float2(a, b);
+                part += rc[c] * a + rc[c + 1] * b;
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+    }
+    if (abort_flag) {
+        if (threadIdx.x == 0) {
+            for (int u = issued; u > issued - FT_NS && u >= P.tlo; --u) mbar_wait(S.bar(ft_slot(P, u)), ft_parity(P, u));
+            atomicExch(&sc->dev_error, 1);
+        }
+        part = 0.f;
+    }
+    decltype(part) acc[1] = {part};
+    grid_reduce<1>(acc, partials, counter, [&](double* tt) {
+        sc->rz_old = sc->rz;
+        sc->rz = tt[0];
+    });
+}
+
 
 // ---- set-up -------------------------------------------------------------------------------------
 
@@ -844,6 +1257,68 @@ unsigned lin_blocks(long long n) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// ---- tensor maps of the fused passes -------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 3-D map of an nx x ny x nz array of `esize`-byte elements, box (boxx, FT_RY, 1): one plane of a
+// tile plus its halo per load.  Elements outside the array read as zero.
+int make_plane_map(CUtensorMap* out, const Dom& D, const void* ptr, CUtensorMapDataType dt, int esize, int boxx) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return ibm_fail(IBM_E_CUDA, "multigrid: cuTensorMapEncodeTiled is not available");
+    alignas(64) CUtensorMap m;
+    cuuint64_t dims[3] = {(cuuint64_t)D.nx, (cuuint64_t)D.ny, (cuuint64_t)D.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)D.nx * esize, (cuuint64_t)D.nx * D.ny * esize};
+    cuuint32_t box[3] = {(cuuint32_t)boxx, (cuuint32_t)FT_RY, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(&m, dt, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return ibm_fail(IBM_E_CUDA, "multigrid: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    memcpy(out, &m, sizeof(m));
+    return IBM_OK;
+}
+
+// Whether the fused passes apply, and their launch shape: tiles of FT_TX x FT_TY and the z-chunk that
+// minimises waves x (chunk + 8 planes of pipeline) with two resident blocks per SM.
+void fused_plan(const LesCtx& c, MG& mg, int sb) {
+    const Dom& D = c.D;
+    bool per = false;
+    for (int f = 0; f < 6; ++f) per = per || D.bc[f] == IBM_BC_PERIODIC;
+    mg.fused = mg.allow_fused && sb == 4 && mg.sweeps == 2 && mg.nlev > 1 && D.flags != nullptr && !per && D.nx % 16 == 0 &&
+               D.nx >= 16 && D.ny >= 2 && D.nz >= 2 && encode_tiled() != nullptr;
+    if (!mg.fused) return;
+    const long long tx = (D.nx + FT_TX - 1) / FT_TX, ty = (D.ny + FT_TY - 1) / FT_TY;
+    const long long slots = 2LL * IBM_NSM;
+    long long best = -1;
+    int best_k = D.nz + (D.nz & 1);
+    for (int ch = 1; ch <= 64; ++ch) {
+        int k = (D.nz + ch - 1) / ch;
+        k += k & 1;
+        if (k < 8 && ch > 1) break;
+        const long long nchunk = (D.nz + k - 1) / k;
+        const long long waves = (tx * ty * nchunk + slots - 1) / slots;
+        const long long cost = waves * (k + 8);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_k = k;
+        }
+    }
+    mg.fz_chunk = best_k;
+    mg.fgrid = dim3((unsigned)tx, (unsigned)ty, (unsigned)((D.nz + best_k - 1) / best_k));
+    mg.tm_r_ptr = nullptr;
+}
+
 // ---- host side of the set-up --------------------------------------------------------------------
 
 struct SetupTmp {
@@ -995,13 +1470,113 @@ int build_next(MGLev& F, MGLev& C, int sb, SetupTmp& t) {
 
 }  // namespace
 
+// Coarse levels of a V-cycle (level 1 holds the restricted residual; on return level 1 holds the
+// coarse correction): descent, coarsest solve and ascent, as separate kernels on the large levels
+// and one cluster launch for the small ones.
+template <class T>
+static int coarse_levels(const LesCtx& c, const MG& mg, SolveScal* sc, cudaStream_t s, int& launches) {
+    const T om = (T)mg.omega;
+    const int SC = mg.sweeps > 0 ? 1 : 0;
+    int tf = mg.nlev;
+    for (int l = 1; l + 1 < mg.nlev; ++l)
+        if (mg.lev[l].M <= MG_TAIL_MAX) { tf = l; break; }
+    const int top = tf < mg.nlev ? tf : mg.nlev - 1;
+    for (int l = 1; l < top; ++l) {
+        const MGLev& L = mg.lev[l];
+        for (int q = 0; q < SC; ++q) {
+            k_gsmooth<T><<<lin_blocks(q == 0 ? L.M : L.M0), 256, 0, s>>>(L, 0, q == 0, sc);
+            k_gsmooth<T><<<lin_blocks(L.M - L.M0), 256, 0, s>>>(L, 1, 0, sc);
+            launches += 2;
+        }
+        k_grestrict<T><<<lin_blocks(mg.lev[l + 1].M), 256, 0, s>>>(L, mg.lev[l + 1], sc);
+        ++launches;
+    }
+    if (tf < mg.nlev) {
+        MGTail M;
+        for (int l = 0; l < IBM_MG_MAXLEV; ++l) M.lev[l] = mg.lev[l];
+        M.first = tf;
+        M.nlev = mg.nlev;
+        M.sweeps = SC;
+        M.coarse_sweeps = mg.coarse_sweeps;
+        M.omega = mg.omega;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(MG_TAIL_CTAS);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = MG_TAIL_CTAS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        IBM_CUDA(cudaLaunchKernelEx(&cfg, k_mg_tail<T>, M, (const SolveScal*)sc));
+        ++launches;
+    } else {
+        k_gcoarsest<T><<<1, 1024, 0, s>>>(mg.lev[mg.nlev - 1], mg.coarse_sweeps, sc);
+        ++launches;
+    }
+    for (int l = top - 1; l >= 1; --l) {
+        const MGLev& L = mg.lev[l];
+        k_gprolong<T><<<lin_blocks(L.M), 256, 0, s>>>(L, mg.lev[l + 1], om, sc);
+        ++launches;
+        for (int q = 0; q < SC; ++q) {
+            k_gsmooth<T><<<lin_blocks(L.M - L.M0), 256, 0, s>>>(L, 1, 0, sc);
+            k_gsmooth<T><<<lin_blocks(L.M0), 256, 0, s>>>(L, 0, 0, sc);
+            launches += 2;
+        }
+    }
+    return IBM_OK;
+}
+
+// V-cycle with the fused fine-grid passes: pre-smoothing + restriction, the coarse levels,
+// prolongation, post-smoothing + (r, z).
+static int vcycle_fused(const LesCtx& c, MG& mg, const float* r, float* z, SolveScal* sc, cudaStream_t s) {
+    if (mg.tm_r_ptr != r) {
+        int rc = make_plane_map(&mg.tm_r, c.D, r, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, FT_RX);
+        if (rc) return rc;
+        mg.tm_r_ptr = r;
+    }
+    alignas(64) CUtensorMap tr, tz, tf;
+    memcpy(&tr, &mg.tm_r, sizeof(tr));
+    memcpy(&tz, &mg.tm_z2, sizeof(tz));
+    memcpy(&tf, &mg.tm_f, sizeof(tf));
+    float* z2 = (float*)mg.z2;
+    const float scale = (float)(c.D.dx * c.D.dx);
+    const MGLev& L1 = mg.lev[1];
+    int launches = 0;
+    prof_begin(c.prof, PS_MG_FINE, s);
+    k_mg_pre_fused<<<mg.fgrid, FT_NT, FT_SMEM, s>>>(c.D, z2, scale, L1, mg.fz_chunk, sc, tr, tf);
+    prof_end(c.prof, PS_MG_FINE, s);
+    ++launches;
+    prof_begin(c.prof, PS_MG_COARSE, s);
+    int rc = coarse_levels<float>(c, mg, sc, s, launches);
+    if (rc) return rc;
+    prof_end(c.prof, PS_MG_COARSE, s);
+    prof_begin(c.prof, PS_MG_TRANSFER, s);
+    k_mg_prolong0_x4<<<lin_blocks((c.D.nx / 4) * (long long)L1.py * L1.pz), 256, 0, s>>>(c.D, z2, L1, (float)mg.omega, sc);
+    prof_end(c.prof, PS_MG_TRANSFER, s);
+    ++launches;
+    prof_begin(c.prof, PS_MG_FINE, s);
+    k_mg_post_fused<<<mg.fgrid, FT_NT, FT_SMEM, s>>>(c.D, z, scale, mg.fz_chunk, sc, c.partials, c.counter, tr, tz, tf);
+    prof_end(c.prof, PS_MG_FINE, s);
+    ++launches;
+    IBM_LAUNCHED("mg_vcycle (fused)");
+    IBM_COUNT(c, launches);
+    return IBM_OK;
+}
+
 void mg_free(MG& mg) {
     for (int l = 1; l < IBM_MG_MAXLEV; ++l) free_level(mg.lev[l]);
+    cudaFree(mg.z2);
+    mg.z2 = nullptr;
     mg.nlev = 1;
 }
 
 int mg_setup(const LesCtx& c, MG& mg, int sb) {
     for (int l = 0; l < IBM_MG_MAXLEV; ++l) memset(&mg.lev[l], 0, sizeof(MGLev));
+    mg.fused = 0;
     MGLev& L0 = mg.lev[0];
     L0.px = c.D.nx;
     L0.py = c.D.ny;
@@ -1025,6 +1600,14 @@ int mg_setup(const LesCtx& c, MG& mg, int sb) {
         if (r2 > 0) break;
         mg.nlev = l + 2;
     }
+    fused_plan(c, mg, sb);
+    if (mg.fused) {
+        IBM_CUDA(cudaFuncSetAttribute(k_mg_pre_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM));
+        IBM_CUDA(cudaFuncSetAttribute(k_mg_post_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM));
+        if ((rc = make_plane_map(&mg.tm_f, c.D, c.D.flags, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, FT_FX))) return rc;
+        MG_ALLOCB(mg.z2, c.D.N * 4);
+        if ((rc = make_plane_map(&mg.tm_z2, c.D, mg.z2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, FT_RX))) return rc;
+    }
     return IBM_OK;
 }
 
@@ -1041,6 +1624,9 @@ int mg_vcycle(const LesCtx& c, const MG& mg, const T* r, T* z, SolveScal* sc, cu
     int launches = 0;
     bool vec = false;
     if constexpr (std::is_same<T, float>::value) vec = x4_ok(c);
+    if constexpr (std::is_same<T, float>::value) {
+        if (mg.fused) return vcycle_fused(c, const_cast<MG&>(mg), r, z, sc, s);
+    }
     auto fine = [&](int col, int zero) {
         prof_begin(c.prof, PS_MG_FINE, s);
         if constexpr (std::is_same<T, float>::value) {

@@ -111,6 +111,7 @@ __global__ void k_reset(SolveScal* sc) {
     sc->iters = 0;
     sc->nonfinite = 0;
     sc->done = 0;
+    sc->dev_error = 0;
 }
 
 // CG, first half: direction p = r + beta p_old (recomputed where a neighbour needs it, so p never
@@ -507,6 +508,8 @@ int pcg_cycles(const LesCtx& c, PoissonWork& w, T* x, int check_every, cudaStrea
 
 }  // namespace
 
+void launch_reset(SolveScal* sc, cudaStream_t s) { k_reset<<<1, 1, 0, s>>>(sc); }
+
 // Residual norms of two candidate iterates in one pass: res2 of xa -> out[0], of xb -> out[1].
 __global__ void __launch_bounds__(256) k_two_residuals(Dom D, const double* __restrict__ b, const double* __restrict__ xa,
                                                        const double* __restrict__ xb, double idx2, double* partials,
@@ -584,6 +587,7 @@ int run_poisson(const LesCtx& c, PoissonWork& w, const double* b, double* x, dou
         IBM_COUNT(c, 1);
         if ((rc = read_scalars(w, s))) return rc;
         const SolveScal h = *w.hsc;
+        if (h.dev_error) return ibm_fail(IBM_E_CUDA, "poisson_solve: a multigrid shared-memory load timed out");
         out.bnorm = sqrt(h.bb);
         out.relres = h.bb > 0.0 ? sqrt(h.res2 / h.bb) : 0.0;
         out.iters = h.iters;

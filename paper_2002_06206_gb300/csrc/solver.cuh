@@ -1,5 +1,7 @@
 // solver.cuh -- the flow solver's internal context and the launchers of its kernels.
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 // Scalars the pressure solve keeps on the device (read by the host only at check points).
@@ -10,7 +12,7 @@ struct SolveScal {
     double ts, tt, ss, rv;              // BiCGStab inner products
     double rz, rz_old;                  // preconditioned CG: (r, z) and its previous value
     int done, iters, restart, nonfinite;
-    int maxit, pad0, pad1, pad2;
+    int maxit, dev_error, pad1, pad2;   // dev_error: a bounded device wait gave up (fused multigrid)
     double part[2];                     // partial sums handed from a fast kernel to its general partner
 };
 
@@ -61,6 +63,16 @@ struct MG {
     int coarse_sweeps;   // symmetric sweeps on the coarsest level
     double omega;        // coarse-correction factor, 0 < omega < 2
     MGLev lev[IBM_MG_MAXLEV];
+    // fused fine-grid passes (FP32, two sweeps, nx a multiple of 4, no periodic axis): tensor maps of
+    // r, z and the flags for the TMA plane loads, made for the vectors last passed to the V-cycle
+    int allow_fused;     // les_params.mg_passes == 0
+    int fused;           // 1: the fused kernels apply to this grid and configuration
+    int fz_chunk;        // planes per z-chunk of a fused launch (even)
+    dim3 fgrid;          // tiles x, tiles y, z-chunks
+    void* z2;            // [N] working precision: pre-smoothed and prolongated z, read by the post-smoothing
+                         // pass (which writes z): no block reads what another block of the pass writes
+    const void* tm_r_ptr;
+    CUtensorMap tm_r, tm_z2, tm_f;
 };
 
 // Crank-Nicolson predictor workspace: BiCGStab vectors over the stacked three components (3N values
@@ -163,6 +175,7 @@ struct PoissonWork {
     long long glaunches;
 };
 int launch_apply64(const LesCtx& c, const double* p, double* Ap, cudaStream_t s);
+void launch_reset(SolveScal* sc, cudaStream_t s);   // clears the solve's device flags
 int launch_two_residuals(const LesCtx& c, const double* b, const double* xa, const double* xb, double* out,
                          cudaStream_t s);
 // learn.cu

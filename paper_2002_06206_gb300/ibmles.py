@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("check_every", C.c_int32), ("inner_tol", C.c_double), ("sor_omega", C.c_double),
                 ("precond", C.c_int32), ("mg_sweeps", C.c_int32), ("mg_omega", C.c_double),
                 ("quick", C.c_double), ("integrator", C.c_int32), ("mom_max_iter", C.c_int32),
-                ("mom_tol", C.c_double)]
+                ("mom_tol", C.c_double), ("mg_passes", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -94,6 +94,9 @@ SIGNATURES = {
                                 C.c_void_p, C.c_void_p]),
     "forces": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "les_num_faces": (C.c_int64, [C.c_void_p]),
+    "poisson_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ibm_probe_fma_rate": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
+    "les_mg_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "les_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "les_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "les_kernel_launches": (C.c_int64, [C.c_void_p]),
@@ -160,6 +163,13 @@ def _stream(stream):
 
 def make_grid(nx, ny, nz, dx=1.0):
     return Grid(nx, ny, nz, 0, dx)
+
+
+def fma_rate(precision=FP64, stream=None):
+    """Measured FMA rate of the current GPU, TFLOP/s."""
+    out = C.c_double()
+    _check(lib().ibm_probe_fma_rate(precision, C.byref(out), _stream(stream)))
+    return out.value
 
 
 def num_faces(nx, ny, nz):
@@ -234,6 +244,7 @@ class Geometry:
             break
         self.n_cut = int(n_cut.value)
         self.n_tests = int(n_tests.value)
+        self.workspace = None           # 48 bytes per cell, needed by the classification only
         self.face_id = self.face_id[:self.n_cut]
         self.t_lo = self.t_lo[:self.n_cut]
         self.t_hi = self.t_hi[:self.n_cut]
@@ -275,14 +286,14 @@ class Solver:
     def __init__(self, grid, nu, dt, bc, u_in=(1.0, 0.0, 0.0), precision=FP64, solver=CG, tol=1e-6,
                  max_iter=100000, check_every=16, inner_tol=1e-4, sor_omega=1.9, csm_on=1, forcing_on=1,
                  geometry=None, precond=NO_PRECOND, mg_sweeps=2, mg_omega=1.6, quick=0.0,
-                 integrator=ADAMS_BASHFORTH, mom_tol=0.0, mom_max_iter=0):
+                 integrator=ADAMS_BASHFORTH, mom_tol=0.0, mom_max_iter=0, mg_passes=0):
         self.grid = grid
         self.N = grid.nx * grid.ny * grid.nz
         self.NF = num_faces(grid.nx, grid.ny, grid.nz)
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.params = Params(nu, dt, (C.c_double * 3)(*u_in), (C.c_int32 * 6)(*bc), csm_on, forcing_on,
                              precision, solver, tol, max_iter, check_every, inner_tol, sor_omega, precond,
-                             mg_sweeps, mg_omega, quick, integrator, mom_max_iter, mom_tol)
+                             mg_sweeps, mg_omega, quick, integrator, mom_max_iter, mom_tol, mg_passes, 0)
         self.geometry = geometry
         h = C.c_void_p()
         _check(lib().les_create(C.byref(grid), C.byref(self.params),
@@ -361,6 +372,16 @@ class Solver:
         _check(lib().forces(self.handle, _ptr(tri, torch.float32), tri.shape[0], _ptr(p, torch.float64),
                             None if u is None else _ptr(u, self.dtype, "u"), out, _stream(stream)))
         return list(out)
+
+    def precond(self, r, z, stream=None):
+        """z = one multigrid V-cycle applied to r (working precision)."""
+        _check(lib().poisson_precond(self.handle, _ptr(r, self.dtype, "r"), _ptr(z, self.dtype, "z"), _stream(stream)))
+
+    def mg_info(self):
+        """(levels, fused fine passes, unknowns per level)."""
+        out = (C.c_int64 * 18)()
+        _check(lib().les_mg_info(self.handle, out, 18))
+        return int(out[0]), bool(out[1]), [int(out[2 + l]) for l in range(min(int(out[0]), 16))]
 
     PROFILE_SLOTS = ("csm", "predict", "forcing", "faces", "rhs", "residual", "cg_dir_spmv", "cg_update",
                      "correct", "sor", "mg_fine", "mg_transfer", "mg_coarse", "momentum")

@@ -361,8 +361,8 @@ def test_ten_steps_fp32_refine64_dirty_sphere_96x48x48(L, precond):
 @pytest.mark.parametrize("quick", [0.0, 0.1])
 def test_ten_steps_ground_cube_plate_ragged(L, quick):
     tri = W.cube_and_plate() * np.float32(0.25)
-    cfg = (131, 64, 37, 8.0 / 4e4, 0.2)
-    u0 = W.initial_fields(W.Config("c", 131, 64, 37, 0, 0, 0, 0, 0, GROUND, seed=3))
+    cfg = (99, 48, 29, 8.0 / 4e4, 0.2)
+    u0 = W.initial_fields(W.Config("c", 99, 48, 29, 0, 0, 0, 0, 0, GROUND, seed=3))
     st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP64, 1e-9, u0, GROUND, quick=quick)
     assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-6
 
@@ -386,8 +386,8 @@ def test_ten_steps_crank_nicolson_quick(L, prec, tol, mom_tol):
 
 def test_ten_steps_crank_nicolson_ground_ragged(L):
     tri = W.cube_and_plate() * np.float32(0.25)
-    cfg = (131, 64, 37, 8.0 / 4e4, 0.2)
-    u0 = W.initial_fields(W.Config("c", 131, 64, 37, 0, 0, 0, 0, 0, GROUND, seed=3))
+    cfg = (99, 48, 29, 8.0 / 4e4, 0.2)
+    u0 = W.initial_fields(W.Config("c", 99, 48, 29, 0, 0, 0, 0, 0, GROUND, seed=3))
     st, ost, _ = _run_pair(L, cfg, tri, 10, L.FP64, 1e-9, u0, GROUND, quick=0.1, integrator=L.CRANK_NICOLSON,
                            mom_tol=1e-13)
     assert rel(st["u"].cpu().numpy(), ost["u"]) <= 1e-6
