@@ -428,22 +428,33 @@ def kernel_groups(solver, torch, st, steps, N, s_bytes, args, tol, peak):
     mean launch time."""
     solver.profile(1)
     torch.cuda.synchronize()
+    iters = 0
     for _ in range(steps):
         s = solver.step(st)
         if s.status != 0:
             raise RuntimeError("profiled step failed: status %d" % s.status)
+        iters += s.iters
     torch.cuda.synchronize()
     prof = solver.profile_read()
     solver.profile(0)
-    fused = solver.mg_info()[1]
+    levels, fused, _ = solver.mg_info()
     bpc = bytes_per_cell(s_bytes, args.integrator, args.mg_sweeps, fused)
+    # The Krylov kernels are launched check_every iterations at a time and return at once when the
+    # solve has converged, so their launch counts include such empty launches: the per-iteration groups
+    # are averaged over the iterations the solves actually ran (the empty launches' few microseconds
+    # stay in the totals).
+    per_iter = {"cg_dir_spmv": 1, "cg_update": 1}
+    if levels > 0:
+        per_iter["mg_fine"] = 2 if fused else 4 * args.mg_sweeps
+        per_iter["mg_transfer"] = 1 if fused else 2
     groups = {}
     for k, (ms_k, n_k) in prof.items():
         if n_k <= 0 or k not in bpc:
             continue
-        gbs = bpc[k] * N / (ms_k / n_k * 1e-3) / 1e9
-        groups[k] = {"launches": n_k, "avg_launch_ms": ms_k / n_k, "bytes_per_launch": bpc[k] * N,
-                     "achieved_gbs": gbs, "frac": gbs / peak}
+        n_eff = min(n_k, per_iter[k] * iters) if k in per_iter and iters > 0 else n_k
+        gbs = bpc[k] * N / (ms_k / n_eff * 1e-3) / 1e9
+        groups[k] = {"launches": n_eff, "launches_incl_empty": n_k, "avg_launch_ms": ms_k / n_eff,
+                     "bytes_per_launch": bpc[k] * N, "achieved_gbs": gbs, "frac": gbs / peak}
     return prof, groups
 
 
@@ -572,27 +583,41 @@ def train_guess(L, torch, args):
 
 
 def learned_vs_plain(L, torch, m, net, train, args, world, stream):
-    """K steps without and K steps with the guess, consecutive windows from the same solver state."""
+    """K steps without a guess, K steps with the bare extrapolation 2 p^n - p^{n-1} (the guess of a
+    network with zero parameters) and K steps with the trained guess: consecutive windows from the same
+    solver state, so the gain of the network itself is the difference of the last two."""
     solver, st = m["_solver"], m["_state"]
     tol = solver.params.tol
     N = m["cells"]
-    ms_plain, st_plain, _ = timed_steps(L, torch, solver, st, args.steps, tol, stream)
-    solver.attach_guess(net)
-    checked_step(L, solver, st, tol)                      # the guess needs p^{n-1}
-    ms_learn, st_learn, _ = timed_steps(L, torch, solver, st, args.steps, tol, stream)
-    solver.attach_guess(None)
-    ms_plain = max_over_ranks(ms_plain, world)
-    ms_learn = max_over_ranks(ms_learn, world)
-    ratios = [s["relres_guess"] / s["relres0"] for s in st_learn if s["relres0"] > 0]
-    return {"workload": m["workload"], "value": N * args.steps * world / (ms_learn * 1e-3) / 1e6,
-            "ms_per_step": ms_learn / args.steps, "solve": solve_summary(st_learn),
-            "guess_used_fraction": float(np.mean([s["guess_used"] for s in st_learn])),
-            "median_initial_residual_ratio": float(np.median(ratios)) if ratios else None,
-            "plain_same_window": {"value": N * args.steps * world / (ms_plain * 1e-3) / 1e6,
-                                  "ms_per_step": ms_plain / args.steps, "solve": solve_summary(st_plain)},
-            "speedup": ms_plain / ms_learn, "train": train,
-            "note": "plain window first, then the learned window, from the same solver state; the network "
-                    "is trained on snapshots of a different workload (%s)" % TRAIN_WORKLOAD}
+
+    def window(guess):
+        solver.attach_guess(guess)
+        if guess is not None:
+            checked_step(L, solver, st, tol)                 # the guess needs p^{n-1}
+        ms, stats, _ = timed_steps(L, torch, solver, st, args.steps, tol, stream)
+        solver.attach_guess(None)
+        ms = max_over_ranks(ms, world)
+        ratios = [s["relres_guess"] / s["relres0"] for s in stats if s["relres0"] > 0]
+        out = {"value": N * args.steps * world / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+               "solve": solve_summary(stats)}
+        if guess is not None:
+            out["guess_used_fraction"] = float(np.mean([s["guess_used"] for s in stats]))
+            out["median_initial_residual_ratio"] = float(np.median(ratios)) if ratios else None
+        return out
+
+    plain = window(None)
+    zero = L.Net(np.zeros(net.n_params, np.float32))
+    extrap = window(zero)
+    zero.close()
+    learned = window(net)
+    learned.update({"workload": m["workload"], "plain_same_window": plain, "extrapolation_same_window": extrap,
+                    "speedup": plain["ms_per_step"] / learned["ms_per_step"],
+                    "speedup_over_extrapolation": extrap["ms_per_step"] / learned["ms_per_step"], "train": train,
+                    "note": "three consecutive windows from the same solver state: no guess, the bare extrapolation "
+                            "2 p^n - p^{n-1} (a network with zero parameters), the trained guess; initial residual "
+                            "ratios are the guess's over p^n's; the network is trained on snapshots of a different "
+                            "workload (%s)" % TRAIN_WORKLOAD})
+    return learned
 
 
 def roofline_of(m, workload):

@@ -133,7 +133,9 @@ int ibm_classify(const ibm_grid* grid, const float* d_tri, int64_t ntri, const i
  * every GPU that loads the library until the process exits; grids and soups whose
  * ibm_classify_workspace_bytes() exceed it are rejected with IBM_E_INVALID before any device work.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.  All calls share the one
+ * that device current) and keeps it for the life of the process; make that first call before any
+ * stream capture.  cudaDeviceReset destroys the device's context and with it that address: after a
+ * reset this entry point must not be called again in the same process.  All calls share the one
  * array: calls that overlap on the GPU (other streams or threads, same device) race and must be
  * serialised by the caller.  Each call re-initialises what it needs, so earlier contents do not
  * matter. */

@@ -570,7 +570,8 @@ int ibm_geom_deadend(const ibm_geom* G) { return G->gp.deadend_on ? 1 : 0; }
 //
 // The scratch lives in a fixed device array of this file.  Its name in host code is only a host-side
 // stand-in, so the device address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and cached; kernels receive that address.
+// device current) and cached; kernels receive that address.  The cache holds for the life of the
+// device's context: a cudaDeviceReset invalidates it (documented in the header).
 
 #include <mutex>
 

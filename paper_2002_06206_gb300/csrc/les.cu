@@ -8,6 +8,9 @@
 // cells next to cut links in a separate general kernel.
 #include "solver.cuh"
 
+#ifndef IBM_FLUX_GEN_MINB
+#define IBM_FLUX_GEN_MINB 4   // the general-cell flux kernels gather from global memory: occupancy pays for small spills
+#endif
 #ifndef IBM_FLUX_MINB
 #define IBM_FLUX_MINB 3
 #endif
@@ -397,7 +400,7 @@ __device__ __forceinline__ void flux_cells(const Dom& D, const FaceLayout& F, co
 // Resident blocks of 256 threads per SM the fast FP32 flux kernels are compiled for (register cap).
 template <class T, bool GENERAL>
 struct FluxOcc {
-    static constexpr int value = (sizeof(T) == 4 && !GENERAL) ? IBM_FLUX_MINB : 1;
+    static constexpr int value = sizeof(T) == 4 ? (GENERAL ? IBM_FLUX_GEN_MINB : IBM_FLUX_MINB) : 1;
 };
 
 template <bool GENERAL, class T>

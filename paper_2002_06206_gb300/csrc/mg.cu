@@ -242,14 +242,21 @@ __device__ __forceinline__ int fine_parts(const Dom& D, const unsigned (&fl)[8],
 // only write their own.
 
 #define FT_TX 48                    // tile along x (a multiple of 16: the flags box starts 16 cells left)
-#define FT_TY 20                    // tile along y (even: level-1 blocks are 2 x 2 x 2)
+#ifndef FT_TY
+#define FT_TY 16                    // tile along y (even: level-1 blocks are 2 x 2 x 2)
+#endif
+#ifndef FT_LA
+#define FT_LA 2                     // planes loaded ahead of the one a step consumes
+#endif
 #define FT_H 4                      // halo
 #define FT_RX (FT_TX + 2 * FT_H)    // r / z box along x (56 floats = 224 bytes)
 #define FT_RY (FT_TY + 2 * FT_H)    // box along y
 #define FT_FX (FT_TX + 32)          // flags box along x (80 bytes), starting 16 cells left of the tile
 #define FT_FOFF 12                  // flags column of r/z column 0
-#define FT_NS 7                     // ring slots: planes t-5 .. t+1
-#define FT_NT 512                   // threads
+#define FT_NS (6 + FT_LA)           // ring slots: planes t-5 .. t+FT_LA
+#define FT_QX (FT_RX / 4)           // 4-cell quads per ring row
+#define FT_NQ (FT_QX * FT_RY)       // quads of the ring plane
+#define FT_NT (((FT_NQ + 31) / 32) * 32)   // threads: one quad each
 #define FT_RBYTES (FT_RX * FT_RY * 4)
 #define FT_FBYTES (FT_FX * FT_RY)
 #define FT_FPAD (((FT_FBYTES + 127) / 128) * 128)
@@ -329,20 +336,57 @@ __device__ __forceinline__ void ft_issue(const Dom& D, const FTSmem& S, const FT
     tma_load3((void*)S.f(s), tf, P.gx0 - FT_FOFF, P.gy0, t, b);
 }
 
-// Gauss-Seidel value of ring cell (rx, ry) of plane t:  (sum of z over the open links - scale r) / dg,
-// dg = open links + the outflow terms.  The interior case (no cut link, not on a domain face) sums the
-// six neighbours as the separate passes do.
-__device__ __forceinline__ float ft_gs(const Dom& D, const FTSmem& S, const FTPos& P, int t, int rx, int ry,
-                                       float scale, const float* zm, const float* zc, const float* zp,
-                                       const float* rc, const uint8_t* fc) {
-    const int c = ry * FT_RX + rx;
-    const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
-    const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-    const float sr = scale * rc[c];
-    if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1) {
-        const float s = ((zc[c - 1] + zc[c + 1]) + (zc[c - FT_RX] + zc[c + FT_RX])) + (zm[c] + zp[c]);
-        return (s - sr) * (1.f / 6.f);
+// Per-thread cells: thread q < FT_NQ owns the quad of 4 consecutive ring cells (ry, 4 qx .. 4 qx + 3),
+// fixed for the whole march; the quads line up with the tile (its x-range starts at ring column 4).
+// Cell masks (bit m for cell m): in the domain; interior (its in-plane neighbours are in the domain,
+// which the plain form of the update needs); within distance e of the tile (the half-sweeps of halo
+// e update those), for e = 0 .. 3.
+struct FTQuad {
+    int c;          // ring index of cell 0
+    int f;          // flags-ring index of cell 0 (a multiple of 4)
+    int gx, gy;     // global coordinates of cell 0
+    int par;        // (gx + gy) & 1
+    int tile;       // index of cell 0 in the tile (tile quads), -1 otherwise
+    unsigned dom, inter, halo;   // halo: 4 bits per e
+};
+
+__device__ __forceinline__ FTQuad ft_quad(const Dom& D, const FTPos& P, int q) {
+    FTQuad a;
+    a.c = a.f = a.gx = a.gy = a.par = 0;
+    a.tile = -1;
+    a.dom = a.inter = a.halo = 0u;
+    if (q >= FT_NQ) return a;
+    const int ry = q / FT_QX, rx = 4 * (q % FT_QX);
+    a.c = ry * FT_RX + rx;
+    a.f = ry * FT_FX + rx + FT_FOFF;
+    a.gx = P.gx0 + rx;
+    a.gy = P.gy0 + ry;
+    a.par = (a.gx + a.gy) & 1;
+    const int dy = max(max(FT_H - ry, ry - (FT_H + FT_TY - 1)), 0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int x = rx + m, gx = a.gx + m;
+        const int dx = max(max(FT_H - x, x - (FT_H + FT_TX - 1)), 0);
+        const bool in = gx >= 0 && gx < D.nx && a.gy >= 0 && a.gy < D.ny;
+        const bool inter = gx > 0 && gx < D.nx - 1 && a.gy > 0 && a.gy < D.ny - 1;
+        const int d = max(dx, dy);
+        a.dom |= (in ? 1u : 0u) << m;
+        a.inter |= (inter ? 1u : 0u) << m;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (in && d <= e) a.halo |= 1u << (4 * e + m);
     }
+    if (dy == 0 && rx >= FT_H && rx < FT_H + FT_TX) a.tile = (ry - FT_H) * FT_TX + (rx - FT_H);
+    return a;
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4e(const float4& v, int m) { return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w)); }
+
+// Gauss-Seidel value of a ring cell in the generic case (a cut link or a domain face next to it):
+// (sum of z over the open links - sr) / dg, dg = open links + the outflow terms.
+__device__ __forceinline__ float ft_gs_generic(const Dom& D, int c, int gx, int gy, int t, unsigned fl, float sr,
+                                               const float* zm, const float* zc, const float* zp) {
     const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
     float s = 0.f, dg = 0.f;
 #pragma unroll
@@ -359,15 +403,10 @@ __device__ __forceinline__ float ft_gs(const Dom& D, const FTSmem& S, const FTPo
     return dg == 0.f ? 0.f : (s - sr) / dg;
 }
 
-// A * z at ring cell (rx, ry) of plane t in the unscaled form  sum_open (z_N - z_P) - d z_P.
-__device__ __forceinline__ float ft_az(const Dom& D, const FTPos& P, int t, int rx, int ry, const float* zm,
-                                       const float* zc, const float* zp, const uint8_t* fc) {
-    const int c = ry * FT_RX + rx;
-    const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
-    const int gx = P.gx0 + rx, gy = P.gy0 + ry;
+// A z at a ring cell in the generic case, unscaled form  sum_open (z_N - z_P) - d z_P.
+__device__ __forceinline__ float ft_az_generic(const Dom& D, int c, int gx, int gy, int t, unsigned fl,
+                                               const float* zm, const float* zc, const float* zp) {
     const float zP = zc[c];
-    if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1)
-        return ((zc[c - 1] + zc[c + 1]) + (zc[c - FT_RX] + zc[c + FT_RX])) + (zm[c] + zp[c]) - 6.f * zP;
     const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
     float s = 0.f;
 #pragma unroll
@@ -382,28 +421,56 @@ __device__ __forceinline__ float ft_az(const Dom& D, const FTPos& P, int t, int 
     return s;
 }
 
-// One half-sweep of colour `col` on plane t over the ring cells within `e` of the tile.  A half-sweep
-// of the k-th kind (k = 1, 2, 3) runs only on planes t >= tlo + k: below that its inputs (the previous
-// half-sweep on plane t - 1) were never formed in this block, and nothing it would produce is needed.
-__device__ __forceinline__ void ft_half_sweep(const Dom& D, const FTSmem& S, const FTPos& P, int t, int col, int e,
-                                              float scale, int kind) {
+// The ring planes of one step: slot of plane t - k for k = 0 .. 5 (one modulo per step).
+struct FTRing {
+    int sl[6];
+    __device__ __forceinline__ FTRing(const FTPos& P, int t) {
+        sl[0] = (t - P.tlo) % FT_NS;
+#pragma unroll
+        for (int k = 1; k < 6; ++k) sl[k] = sl[k - 1] == 0 ? FT_NS - 1 : sl[k - 1] - 1;
+    }
+};
+
+// One half-sweep of colour `col` on plane t = step - k (ring slot R.sl[k]) over the thread's cells
+// within `e` of the tile.  The k-th half-sweep of a pass runs only on planes t >= tlo + k: below that
+// its inputs (the previous half-sweep on plane t - 1) were never formed in this block, and nothing it
+// would produce is needed.  The quad's two cells of colour col are d and d + 2; a cell with no cut
+// link whose neighbours lie in the domain takes the six-neighbour sum from 16-byte loads.
+__device__ __forceinline__ void ft_half_sweep(const Dom& D, const FTSmem& S, const FTPos& P, const FTQuad& Q,
+                                              const FTRing& R, int k, int t, int col, int e, float scale, int kind) {
     if (t < P.tlo + kind || t < 0 || t >= D.nz) return;
-    const int s = ft_slot(P, t);
-    float* zc = S.z(s);
-    const float* zm = S.z(ft_slot(P, t - 1));     // planes outside the domain are never read (links closed)
-    const float* zp = S.z(ft_slot(P, t + 1));
-    const float* rc = S.r(s);
-    const uint8_t* fc = S.f(s);
-    const int rlo = FT_H - e, rhi = FT_H + FT_TY + e;
-    const int clo = FT_H - e, chi = FT_H + FT_TX + e;
-    const int npr = FT_RX / 2;                      // cell pairs per ring row
-    const int n = npr * (rhi - rlo);
-    for (int q = threadIdx.x; q < n; q += FT_NT) {
-        const int ry = rlo + q / npr, pr = q % npr;
-        const int rx = 2 * pr + ((P.gx0 + P.gy0 + ry + t + col) & 1);
-        const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-        if (rx < clo || rx >= chi || gx < 0 || gx >= D.nx || gy < 0 || gy >= D.ny) continue;
-        zc[ry * FT_RX + rx] = ft_gs(D, S, P, t, rx, ry, scale, zm, zc, zp, rc, fc);
+    const int d = (col + Q.par + t) & 1;
+    const unsigned act = (Q.halo >> (4 * e)) & (5u << d);
+    if (!act) return;
+    float* zc = S.z(R.sl[k]);
+    const float* zm = S.z(R.sl[k + 1]);           // planes outside the domain are never read (links closed)
+    const float* zp = S.z(k > 0 ? R.sl[k - 1] : R.sl[k]);
+    const float* rc = S.r(R.sl[k]);
+    const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(R.sl[k]) + Q.f);
+    const bool tint = t > 0 && t < D.nz - 1;
+    const int c = Q.c;
+    const float4 z4 = lds4(zc + c), r4 = lds4(rc + c);
+    const float4 ym = lds4(zc + c - FT_RX), yp = lds4(zc + c + FT_RX);
+    const float4 zl = lds4(zm + c), zu = lds4(zp + c);
+    const bool odd = d != 0;
+    // cells A = d and B = d + 2 and their x-neighbours (the cell left of the quad and the one right of
+    // it lie in the same ring row: an active quad is never in the ring's first or last column)
+    const float left = zc[c - 1], right = zc[c + 4];
+    const float xa_l = odd ? z4.x : left, xa_r = odd ? z4.z : z4.y;
+    const float xb_l = xa_r, xb_r = odd ? right : z4.w;
+    const float sa = ((xa_l + xa_r) + ((odd ? ym.y : ym.x) + (odd ? yp.y : yp.x))) + ((odd ? zl.y : zl.x) + (odd ? zu.y : zu.x));
+    const float sb = ((xb_l + xb_r) + ((odd ? ym.w : ym.z) + (odd ? yp.w : yp.z))) + ((odd ? zl.w : zl.z) + (odd ? zu.w : zu.z));
+    const float ra = odd ? r4.y : r4.x, rb = odd ? r4.w : r4.z;
+    const unsigned fa = (fl4 >> (8 * d)) & 0xffu, fb = (fl4 >> (8 * (d + 2))) & 0xffu;
+    if ((act >> d) & 1u) {
+        zc[c + d] = (fa == 0u && tint && ((Q.inter >> d) & 1u))
+                        ? (sa - scale * ra) * (1.f / 6.f)
+                        : ft_gs_generic(D, c + d, Q.gx + d, Q.gy, t, fa, scale * ra, zm, zc, zp);
+    }
+    if ((act >> (d + 2)) & 1u) {
+        zc[c + d + 2] = (fb == 0u && tint && ((Q.inter >> (d + 2)) & 1u))
+                            ? (sb - scale * rb) * (1.f / 6.f)
+                            : ft_gs_generic(D, c + d + 2, Q.gx + d + 2, Q.gy, t, fb, scale * rb, zm, zc, zp);
     }
 }
 
@@ -426,40 +493,49 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_pre_fused(Dom D, float* __restr
     P.tlo = k0 - 4;
     const int thi = k1 + 3;
     float* __restrict__ b1 = (float*)C1.b;
+    const FTQuad Q = ft_quad(D, P, threadIdx.x);
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < FT_NS; ++s) mbar_init(S.bar(s), 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) ft_issue(D, S, P, P.tlo, false, &tmr, nullptr, &tmf);
-    int issued = P.tlo;
-    for (int t = P.tlo; t <= thi; ++t) {
-        if (threadIdx.x == 0 && t + 1 <= thi) {
-            ft_issue(D, S, P, t + 1, false, &tmr, nullptr, &tmf);
-            issued = t + 1;
+    int issued = P.tlo - 1;
+    if (threadIdx.x == 0)
+        for (int u = P.tlo; u < P.tlo + FT_LA && u <= thi; ++u) {
+            ft_issue(D, S, P, u, false, &tmr, nullptr, &tmf);
+            issued = u;
         }
-        if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
+    for (int t = P.tlo; t <= thi; ++t) {
+        if (threadIdx.x == 0) {
+            if (t + FT_LA <= thi) {
+                ft_issue(D, S, P, t + FT_LA, false, &tmr, nullptr, &tmf);
+                issued = t + FT_LA;
+            }
+            if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
+        }
         __syncthreads();
         if (abort_flag) break;
+        const FTRing R(P, t);
         // h1 on plane t: z = -scale r / dg on colour 0, 0 on colour 1 (z = 0 before the first pass)
-        if (t >= 0 && t < D.nz) {
-            const int s = ft_slot(P, t);
-            float* zc = S.z(s);
-            const float* rc = S.r(s);
-            const uint8_t* fc = S.f(s);
-            for (int c = threadIdx.x; c < FT_RX * FT_RY; c += FT_NT) {
-                const int ry = c / FT_RX, rx = c % FT_RX;
-                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-                zc[c] = 0.f;
-                if (gx < 0 || gx >= D.nx || gy < 0 || gy >= D.ny || ((gx + gy + t) & 1)) continue;
-                const unsigned fl = fc[ry * FT_FX + rx + FT_FOFF];
-                float dg = 0.f;
-                if (fl == 0u && gx > 0 && gx < D.nx - 1 && gy > 0 && gy < D.ny - 1 && t > 0 && t < D.nz - 1) {
-                    zc[c] = (0.f - scale * rc[c]) * (1.f / 6.f);
+        if (t >= 0 && t < D.nz && threadIdx.x < FT_NQ) {
+            const int s = R.sl[0];
+            const float4 r4 = lds4(S.r(s) + Q.c);
+            const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(s) + Q.f);
+            const bool tint = t > 0 && t < D.nz - 1;
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                v[m] = 0.f;
+                if (!((Q.dom >> m) & 1u) || ((Q.par + m + t) & 1)) continue;
+                const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
+                const float sr = scale * f4e(r4, m);
+                if (fl == 0u && tint && ((Q.inter >> m) & 1u)) {
+                    v[m] = (0.f - sr) * (1.f / 6.f);
                     continue;
                 }
-                const int g[3] = {gx, gy, t}, n[3] = {D.nx, D.ny, D.nz};
+                const int g[3] = {Q.gx + m, Q.gy, t}, n[3] = {D.nx, D.ny, D.nz};
+                float dg = 0.f;
 #pragma unroll
                 for (int b = 0; b < 6; ++b) {
                     const int a = b >> 1, sd = (b & 1) ? 1 : -1;
@@ -467,77 +543,92 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_pre_fused(Dom D, float* __restr
                     if (in && !(fl & (1u << b))) dg += 1.f;
                     else if (!in && D.bc[b] == IBM_BC_OUTFLOW) dg += 2.f;
                 }
-                zc[c] = dg == 0.f ? 0.f : (0.f - scale * rc[c]) / dg;
+                v[m] = dg == 0.f ? 0.f : (0.f - sr) / dg;
             }
+            *reinterpret_cast<float4*>(S.z(s) + Q.c) = make_float4(v[0], v[1], v[2], v[3]);
         }
         __syncthreads();
-        ft_half_sweep(D, S, P, t - 1, 1, 3, scale, 1);
+        ft_half_sweep(D, S, P, Q, R, 1, t - 1, 1, 3, scale, 1);
         __syncthreads();
-        ft_half_sweep(D, S, P, t - 2, 0, 2, scale, 2);
+        ft_half_sweep(D, S, P, Q, R, 2, t - 2, 0, 2, scale, 2);
         __syncthreads();
-        ft_half_sweep(D, S, P, t - 3, 1, 1, scale, 3);
+        ft_half_sweep(D, S, P, Q, R, 3, t - 3, 1, 1, scale, 3);
         __syncthreads();
         // plane t-3 is final: store the tile; residual of plane t-4 (its neighbours are final)
         const int tw = t - 3, tr = t - 4;
-        if (tw >= k0 && tw < k1) {
-            const float* zc = S.z(ft_slot(P, tw));
-            for (int q = threadIdx.x; q < FT_TY * (FT_TX / 4); q += FT_NT) {
-                const int ry = FT_H + q / (FT_TX / 4), rx = FT_H + 4 * (q % (FT_TX / 4));
-                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-                if (gx >= D.nx || gy >= D.ny) continue;
-                const float* src = zc + ry * FT_RX + rx;
-                *reinterpret_cast<float4*>(z + gx + (long long)D.sy * gy + D.sz * tw) =
-                    make_float4(src[0], src[1], src[2], src[3]);
-            }
-        }
+        if (tw >= k0 && tw < k1 && Q.tile >= 0 && Q.dom == 0xfu)
+            *reinterpret_cast<float4*>(z + Q.gx + (long long)D.sy * Q.gy + D.sz * tw) = lds4(S.z(R.sl[3]) + Q.c);
         if (tr >= k0 && tr < k1) {
-            const int s = ft_slot(P, tr);
-            const float* zc = S.z(s);
-            const float* zm = S.z(ft_slot(P, tr - 1));
-            const float* zp = S.z(ft_slot(P, tr + 1));
-            const float* rc = S.r(s);
-            const uint8_t* fc = S.f(s);
-            float* res = S.res(tr & 1);
-            for (int q = threadIdx.x; q < FT_TX * FT_TY; q += FT_NT) {
-                const int ry = FT_H + q / FT_TX, rx = FT_H + q % FT_TX;
-                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-                float v = 0.f;
-                if (gx < D.nx && gy < D.ny) v = scale * rc[ry * FT_RX + rx] - ft_az(D, P, tr, rx, ry, zm, zc, zp, fc);
-                res[q] = v;
+            if (Q.tile >= 0) {
+                const int s = R.sl[4];
+                const float* zc = S.z(s);
+                const float* zm = S.z(R.sl[5]);
+                const float* zp = S.z(R.sl[3]);
+                const int c = Q.c;
+                const float4 z4 = lds4(zc + c), r4 = lds4(S.r(s) + c);
+                const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(s) + Q.f);
+                const bool tint = tr > 0 && tr < D.nz - 1;
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+                if (Q.dom) {
+                    const float4 ym = lds4(zc + c - FT_RX), yp = lds4(zc + c + FT_RX);
+                    const float4 zl = lds4(zm + c), zu = lds4(zp + c);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
+                        float az;
+                        if (fl == 0u && tint && ((Q.inter >> m) & 1u)) {
+                            const float xm = m == 0 ? zc[c - 1] : f4e(z4, m - 1);
+                            const float xp = m == 3 ? zc[c + 4] : f4e(z4, m + 1);
+                            az = ((xm + xp) + (f4e(ym, m) + f4e(yp, m))) + (f4e(zl, m) + f4e(zu, m)) - 6.f * f4e(z4, m);
+                        } else {
+                            az = ft_az_generic(D, c + m, Q.gx + m, Q.gy, tr, fl, zm, zc, zp);
+                        }
+                        v[m] = scale * f4e(r4, m) - az;
+                    }
+                }
+                *reinterpret_cast<float4*>(S.res(tr & 1) + Q.tile) = make_float4(v[0], v[1], v[2], v[3]);
             }
             if ((tr & 1) || tr == D.nz - 1) {
                 __syncthreads();
                 // restriction: the level-1 blocks of planes (tr & ~1, tr | 1)
                 const int ke = tr & ~1;
                 const int Z = ke >> 1;
-                const unsigned both = (ke + 1 < D.nz) ? 1u : 0u;
-                const uint8_t* fe = S.f(ft_slot(P, ke));
-                const uint8_t* fo = S.f(ft_slot(P, ke + 1 < D.nz ? ke + 1 : ke));
+                const bool both = ke + 1 < D.nz;
+                // tr odd: the pair is (tr - 1, tr) in slots 5, 4; tr even (the last plane of an odd count): tr alone
+                const uint8_t* fe = S.f((tr & 1) ? R.sl[5] : R.sl[4]);
+                const uint8_t* fo = both ? S.f(R.sl[4]) : fe;
+                const float* re = S.res(0);
+                const float* ro = S.res(1);
                 for (int q = threadIdx.x; q < (FT_TX / 2) * (FT_TY / 2); q += FT_NT) {
                     const int bx = q % (FT_TX / 2), by = q / (FT_TX / 2);
                     const int X = (P.x0 >> 1) + bx, Y = (P.y0 >> 1) + by;
                     if (X >= C1.px || Y >= C1.py) continue;
+                    const bool yok = 2 * Y + 1 < D.ny;           // x: nx is even, so both columns exist
                     unsigned fl[8];
                     float rv[8];
                     unsigned in = 0;
+                    const int fi = (FT_H + 2 * by) * FT_FX + FT_H + 2 * bx + FT_FOFF;
+                    const int ri = (2 * by) * FT_TX + 2 * bx;
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
                         const int di = m & 1, dj = (m >> 1) & 1, dk = m >> 2;
-                        const int gx = 2 * X + di, gy = 2 * Y + dj;
-                        const bool ok = gx < D.nx && gy < D.ny && (dk == 0 || both);
-                        const int rx = FT_H + 2 * bx + di, ry = FT_H + 2 * by + dj;
-                        fl[m] = ok ? (unsigned)(dk ? fo : fe)[ry * FT_FX + rx + FT_FOFF] : 0u;
-                        rv[m] = ok ? S.res(dk)[(2 * by + dj) * FT_TX + 2 * bx + di] : 0.f;
+                        const bool ok = (dj == 0 || yok) && (dk == 0 || both);
+                        fl[m] = ok ? (unsigned)(dk ? fo : fe)[fi + dj * FT_FX + di] : 0u;
+                        rv[m] = ok ? (dk ? ro : re)[ri + dj * FT_TX + di] : 0.f;
                         in |= (ok ? 1u : 0u) << m;
                     }
                     int part[8];
                     const int np = fine_parts(D, fl, in, part);
+                    const int o = C1.off[X + (long long)C1.px * (Y + (long long)C1.py * Z)];
+                    if (np == 1) {
+                        b1[o] = ((rv[0] + rv[1]) + (rv[2] + rv[3])) + ((rv[4] + rv[5]) + (rv[6] + rv[7]));
+                        continue;
+                    }
                     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
 #pragma unroll
                         for (int s2 = 0; s2 < 8; ++s2) acc[s2] += part[m] == s2 ? rv[m] : 0.f;
-                    const int o = C1.off[X + (long long)C1.px * (Y + (long long)C1.py * Z)];
 #pragma unroll
                     for (int s2 = 0; s2 < 8; ++s2)
                         if (s2 < np) b1[o + s2] = acc[s2];
@@ -574,50 +665,46 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_post_fused(Dom D, float* __rest
     const int k0 = blockIdx.z * kchunk, k1 = min(D.nz, k0 + kchunk);
     P.tlo = k0 - 4;
     const int thi = k1 + 3;
+    const FTQuad Q = ft_quad(D, P, threadIdx.x);
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < FT_NS; ++s) mbar_init(S.bar(s), 1);
         fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) ft_issue(D, S, P, P.tlo, true, &tmr, &tmz, &tmf);
-    int issued = P.tlo;
+    int issued = P.tlo - 1;
+    if (threadIdx.x == 0)
+        for (int u = P.tlo; u < P.tlo + FT_LA && u <= thi; ++u) {
+            ft_issue(D, S, P, u, true, &tmr, &tmz, &tmf);
+            issued = u;
+        }
     float part = 0.f;
     for (int t = P.tlo; t <= thi; ++t) {
-        if (threadIdx.x == 0 && t + 1 <= thi) {
-            ft_issue(D, S, P, t + 1, true, &tmr, &tmz, &tmf);
-            issued = t + 1;
+        if (threadIdx.x == 0) {
+            if (t + FT_LA <= thi) {
+                ft_issue(D, S, P, t + FT_LA, true, &tmr, &tmz, &tmf);
+                issued = t + FT_LA;
+            }
+            if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
         }
-        if (!mbar_wait(S.bar(ft_slot(P, t)), ft_parity(P, t))) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
-        ft_half_sweep(D, S, P, t - 1, 1, 3, scale, 1);
+        const FTRing R(P, t);
+        ft_half_sweep(D, S, P, Q, R, 1, t - 1, 1, 3, scale, 1);
         __syncthreads();
-        ft_half_sweep(D, S, P, t - 2, 0, 2, scale, 2);
+        ft_half_sweep(D, S, P, Q, R, 2, t - 2, 0, 2, scale, 2);
         __syncthreads();
-        ft_half_sweep(D, S, P, t - 3, 1, 1, scale, 3);
+        ft_half_sweep(D, S, P, Q, R, 3, t - 3, 1, 1, scale, 3);
         __syncthreads();
-        // last half-sweep on plane t-4 (colour 0, the tile only); each thread then stores its pair
-        // of cells and adds r z of both to the product
+        // last half-sweep on plane t-4 (colour 0, the tile only); each thread then stores its quad and
+        // adds r z of its four cells to the product
         const int tf = t - 4;
-        if (tf >= k0 && tf < k1) {
-            const int s = ft_slot(P, tf);
-            float* zc = S.z(s);
-            const float* zm = S.z(ft_slot(P, tf - 1));
-            const float* zp = S.z(ft_slot(P, tf + 1));
-            const float* rc = S.r(s);
-            const uint8_t* fc = S.f(s);
-            for (int q = threadIdx.x; q < FT_TY * (FT_TX / 2); q += FT_NT) {
-                const int ry = FT_H + q / (FT_TX / 2), rx = FT_H + 2 * (q % (FT_TX / 2));
-                const int gx = P.gx0 + rx, gy = P.gy0 + ry;
-                if (gx >= D.nx || gy >= D.ny) continue;
-                const int m = (gx + gy + tf) & 1;          // the colour-0 cell of the pair is rx + m
-                const int c = ry * FT_RX + rx;
-                zc[c + m] = ft_gs(D, S, P, tf, rx + m, ry, scale, zm, zc, zp, rc, fc);
-                const float a = zc[c], b = zc[c + 1];
-                *reinterpret_cast<float2*>(z + gx + (long long)D.sy * gy + D.sz * tf) = make_float2(a, b);
-                part += rc[c] * a + rc[c + 1] * b;
-            }
+        if (tf >= k0 && tf < k1 && Q.tile >= 0 && Q.dom == 0xfu) {
+            ft_half_sweep(D, S, P, Q, R, 4, tf, 0, 0, scale, 4);
+            const int s = R.sl[4];
+            const float4 z4 = lds4(S.z(s) + Q.c), r4 = lds4(S.r(s) + Q.c);
+            *reinterpret_cast<float4*>(z + Q.gx + (long long)D.sy * Q.gy + D.sz * tf) = z4;
+            part += (r4.x * z4.x + r4.y * z4.y) + (r4.z * z4.z + r4.w * z4.w);
         }
         fence_proxy_async();
         __syncthreads();
@@ -635,7 +722,6 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_post_fused(Dom D, float* __rest
         sc->rz = tt[0];
     });
 }
-
 
 // ---- set-up -------------------------------------------------------------------------------------
 
