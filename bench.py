@@ -385,7 +385,7 @@ def make_solver(L, torch, name, args, precision=None, geo=None, own_scheme=False
     prec = cfg.precision if precision is None else precision
     solver = L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=prec, solver=L.CG,
                       tol=cfg.tol if prec != L.FP64 else (cfg.tol if name == FP64_SMALL else 1e-10),
-                      max_iter=100000, check_every=args.check_every, inner_tol=args.inner_tol,
+                      max_iter=2000, check_every=args.check_every, inner_tol=args.inner_tol,
                       csm_on=cfg.csm_on, forcing_on=cfg.forcing_on, geometry=geo,
                       precond=L.MULTIGRID if args.precond == "mg" else L.NO_PRECOND,
                       quick=quick, integrator=L.CRANK_NICOLSON if integ == 1 else L.ADAMS_BASHFORTH,
@@ -781,7 +781,7 @@ def main():
     ap.add_argument("--quick", type=float, default=0.1, help="QUICK fraction of the advected face value")
     ap.add_argument("--mg-sweeps", type=int, default=2, help="red-black sweeps before and after each coarse correction")
     ap.add_argument("--mg-omega", type=float, default=1.6, help="multigrid coarse-correction factor")
-    ap.add_argument("--inner-tol", type=float, default=1e-5,
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
                     help="FP32 inner solve: residual reduction per FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
