@@ -734,6 +734,9 @@ def run_ours(args):
         fp64[SECONDARY]["roofline"] = {k: v for k, v in roofline_of(f3, SECONDARY).items() if k not in ("shares",)}
         release(f3)
         torch.cuda.empty_cache()
+        # the arithmetic roofs beside the HBM roof: measured FMA rates (2 flops per FMA)
+        fp64["fma_tflops"] = {"fp64": L.fma_rate(L.FP64, stream), "fp32": L.fma_rate(L.FP32_REFINE64, stream),
+                              "note": "independent FMA chains on every SM, best of three launches"}
 
     line = None
     if rank == 0:

@@ -438,16 +438,22 @@ struct FTRing {
 // link whose neighbours lie in the domain takes the six-neighbour sum from 16-byte loads.
 __device__ __forceinline__ void ft_half_sweep(const Dom& D, const FTSmem& S, const FTPos& P, const FTQuad& Q,
                                               const FTRing& R, int k, int t, int col, int e, float scale, int kind) {
-    if (t < P.tlo + kind || t < 0 || t >= D.nz) return;
+    if (t < P.tlo + kind || t < 0 || t >= D.nz) return;     // the same for the whole block
     const int d = (col + Q.par + t) & 1;
     const unsigned act = (Q.halo >> (4 * e)) & (5u << d);
-    if (!act) return;
     float* zc = S.z(R.sl[k]);
     const float* zm = S.z(R.sl[k + 1]);           // planes outside the domain are never read (links closed)
     const float* zp = S.z(k > 0 ? R.sl[k - 1] : R.sl[k]);
     const float* rc = S.r(R.sl[k]);
     const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(R.sl[k]) + Q.f);
     const bool tint = t > 0 && t < D.nz - 1;
+    const unsigned fa = (fl4 >> (8 * d)) & 0xffu, fb = (fl4 >> (8 * (d + 2))) & 0xffu;
+    const bool onA = (act >> d) & 1u, onB = (act >> (d + 2)) & 1u;
+    const bool plainA = fa == 0u && tint && ((Q.inter >> d) & 1u);
+    const bool plainB = fb == 0u && tint && ((Q.inter >> (d + 2)) & 1u);
+    // a warp without a generic cell skips the generic form altogether
+    const bool generic = __any_sync(0xffffffffu, (onA && !plainA) || (onB && !plainB));
+    if (!act) return;
     const int c = Q.c;
     const float4 z4 = lds4(zc + c), r4 = lds4(rc + c);
     const float4 ym = lds4(zc + c - FT_RX), yp = lds4(zc + c + FT_RX);
@@ -461,17 +467,13 @@ __device__ __forceinline__ void ft_half_sweep(const Dom& D, const FTSmem& S, con
     const float sa = ((xa_l + xa_r) + ((odd ? ym.y : ym.x) + (odd ? yp.y : yp.x))) + ((odd ? zl.y : zl.x) + (odd ? zu.y : zu.x));
     const float sb = ((xb_l + xb_r) + ((odd ? ym.w : ym.z) + (odd ? yp.w : yp.z))) + ((odd ? zl.w : zl.z) + (odd ? zu.w : zu.z));
     const float ra = odd ? r4.y : r4.x, rb = odd ? r4.w : r4.z;
-    const unsigned fa = (fl4 >> (8 * d)) & 0xffu, fb = (fl4 >> (8 * (d + 2))) & 0xffu;
-    if ((act >> d) & 1u) {
-        zc[c + d] = (fa == 0u && tint && ((Q.inter >> d) & 1u))
-                        ? (sa - scale * ra) * (1.f / 6.f)
-                        : ft_gs_generic(D, c + d, Q.gx + d, Q.gy, t, fa, scale * ra, zm, zc, zp);
+    float va = (sa - scale * ra) * (1.f / 6.f), vb = (sb - scale * rb) * (1.f / 6.f);
+    if (generic) {
+        if (onA && !plainA) va = ft_gs_generic(D, c + d, Q.gx + d, Q.gy, t, fa, scale * ra, zm, zc, zp);
+        if (onB && !plainB) vb = ft_gs_generic(D, c + d + 2, Q.gx + d + 2, Q.gy, t, fb, scale * rb, zm, zc, zp);
     }
-    if ((act >> (d + 2)) & 1u) {
-        zc[c + d + 2] = (fb == 0u && tint && ((Q.inter >> (d + 2)) & 1u))
-                            ? (sb - scale * rb) * (1.f / 6.f)
-                            : ft_gs_generic(D, c + d + 2, Q.gx + d + 2, Q.gy, t, fb, scale * rb, zm, zc, zp);
-    }
+    if (onA) zc[c + d] = va;
+    if (onB) zc[c + d + 2] = vb;
 }
 
 // Pre-smoothing (from z = 0, colours 0, 1, 0, 1) + restriction of  scale r - A z  to the parts of the
@@ -518,34 +520,41 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_pre_fused(Dom D, float* __restr
         if (abort_flag) break;
         const FTRing R(P, t);
         // h1 on plane t: z = -scale r / dg on colour 0, 0 on colour 1 (z = 0 before the first pass)
-        if (t >= 0 && t < D.nz && threadIdx.x < FT_NQ) {
+        if (t >= 0 && t < D.nz) {
             const int s = R.sl[0];
             const float4 r4 = lds4(S.r(s) + Q.c);
             const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(s) + Q.f);
             const bool tint = t > 0 && t < D.nz - 1;
-            float v[4];
+            unsigned on = 0u, gen = 0u;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                v[m] = 0.f;
-                if (!((Q.dom >> m) & 1u) || ((Q.par + m + t) & 1)) continue;
-                const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
-                const float sr = scale * f4e(r4, m);
-                if (fl == 0u && tint && ((Q.inter >> m) & 1u)) {
-                    v[m] = (0.f - sr) * (1.f / 6.f);
-                    continue;
-                }
-                const int g[3] = {Q.gx + m, Q.gy, t}, n[3] = {D.nx, D.ny, D.nz};
-                float dg = 0.f;
-#pragma unroll
-                for (int b = 0; b < 6; ++b) {
-                    const int a = b >> 1, sd = (b & 1) ? 1 : -1;
-                    const bool in = g[a] + sd >= 0 && g[a] + sd < n[a];
-                    if (in && !(fl & (1u << b))) dg += 1.f;
-                    else if (!in && D.bc[b] == IBM_BC_OUTFLOW) dg += 2.f;
-                }
-                v[m] = dg == 0.f ? 0.f : (0.f - sr) / dg;
+                const bool o = ((Q.dom >> m) & 1u) && !((Q.par + m + t) & 1);
+                const bool plain = ((fl4 >> (8 * m)) & 0xffu) == 0u && tint && ((Q.inter >> m) & 1u);
+                on |= (o ? 1u : 0u) << m;
+                gen |= (o && !plain ? 1u : 0u) << m;
             }
-            *reinterpret_cast<float4*>(S.z(s) + Q.c) = make_float4(v[0], v[1], v[2], v[3]);
+            float v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = ((on >> m) & 1u) ? (0.f - scale * f4e(r4, m)) * (1.f / 6.f) : 0.f;
+            if (__any_sync(0xffffffffu, gen != 0u)) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (!((gen >> m) & 1u)) continue;
+                    const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
+                    const int g[3] = {Q.gx + m, Q.gy, t}, n[3] = {D.nx, D.ny, D.nz};
+                    float dg = 0.f;
+#pragma unroll
+                    for (int b = 0; b < 6; ++b) {
+                        const int a = b >> 1, sd = (b & 1) ? 1 : -1;
+                        const bool in = g[a] + sd >= 0 && g[a] + sd < n[a];
+                        if (in && !(fl & (1u << b))) dg += 1.f;
+                        else if (!in && D.bc[b] == IBM_BC_OUTFLOW) dg += 2.f;
+                    }
+                    v[m] = dg == 0.f ? 0.f : (0.f - scale * f4e(r4, m)) / dg;
+                }
+            }
+            if (threadIdx.x < FT_NQ)
+                *reinterpret_cast<float4*>(S.z(s) + Q.c) = make_float4(v[0], v[1], v[2], v[3]);
         }
         __syncthreads();
         ft_half_sweep(D, S, P, Q, R, 1, t - 1, 1, 3, scale, 1);
@@ -559,34 +568,40 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_pre_fused(Dom D, float* __restr
         if (tw >= k0 && tw < k1 && Q.tile >= 0 && Q.dom == 0xfu)
             *reinterpret_cast<float4*>(z + Q.gx + (long long)D.sy * Q.gy + D.sz * tw) = lds4(S.z(R.sl[3]) + Q.c);
         if (tr >= k0 && tr < k1) {
-            if (Q.tile >= 0) {
+            {
                 const int s = R.sl[4];
                 const float* zc = S.z(s);
                 const float* zm = S.z(R.sl[5]);
                 const float* zp = S.z(R.sl[3]);
                 const int c = Q.c;
-                const float4 z4 = lds4(zc + c), r4 = lds4(S.r(s) + c);
                 const unsigned fl4 = *reinterpret_cast<const unsigned*>(S.f(s) + Q.f);
                 const bool tint = tr > 0 && tr < D.nz - 1;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                if (Q.dom) {
-                    const float4 ym = lds4(zc + c - FT_RX), yp = lds4(zc + c + FT_RX);
-                    const float4 zl = lds4(zm + c), zu = lds4(zp + c);
+                const bool tq = Q.tile >= 0 && Q.dom != 0u;
+                unsigned gen = 0u;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const unsigned fl = (fl4 >> (8 * m)) & 0xffu;
-                        float az;
-                        if (fl == 0u && tint && ((Q.inter >> m) & 1u)) {
-                            const float xm = m == 0 ? zc[c - 1] : f4e(z4, m - 1);
-                            const float xp = m == 3 ? zc[c + 4] : f4e(z4, m + 1);
-                            az = ((xm + xp) + (f4e(ym, m) + f4e(yp, m))) + (f4e(zl, m) + f4e(zu, m)) - 6.f * f4e(z4, m);
-                        } else {
-                            az = ft_az_generic(D, c + m, Q.gx + m, Q.gy, tr, fl, zm, zc, zp);
+                for (int m = 0; m < 4; ++m)
+                    if (tq && !(((fl4 >> (8 * m)) & 0xffu) == 0u && tint && ((Q.inter >> m) & 1u))) gen |= 1u << m;
+                // a warp without a generic cell skips the generic form altogether
+                const bool generic = __any_sync(0xffffffffu, gen != 0u);
+                if (Q.tile >= 0) {
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (Q.dom) {
+                        const float4 z4 = lds4(zc + c), r4 = lds4(S.r(s) + c);
+                        const float4 ym = lds4(zc + c - FT_RX), yp = lds4(zc + c + FT_RX);
+                        const float4 zl = lds4(zm + c), zu = lds4(zp + c);
+                        const float left = zc[c - 1], right = zc[c + 4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const float xm = m == 0 ? left : f4e(z4, m - 1);
+                            const float xp = m == 3 ? right : f4e(z4, m + 1);
+                            float az = ((xm + xp) + (f4e(ym, m) + f4e(yp, m))) + (f4e(zl, m) + f4e(zu, m)) - 6.f * f4e(z4, m);
+                            if (generic && ((gen >> m) & 1u))
+                                az = ft_az_generic(D, c + m, Q.gx + m, Q.gy, tr, (fl4 >> (8 * m)) & 0xffu, zm, zc, zp);
+                            v[m] = scale * f4e(r4, m) - az;
                         }
-                        v[m] = scale * f4e(r4, m) - az;
                     }
+                    *reinterpret_cast<float4*>(S.res(tr & 1) + Q.tile) = make_float4(v[0], v[1], v[2], v[3]);
                 }
-                *reinterpret_cast<float4*>(S.res(tr & 1) + Q.tile) = make_float4(v[0], v[1], v[2], v[3]);
             }
             if ((tr & 1) || tr == D.nz - 1) {
                 __syncthreads();
@@ -699,8 +714,10 @@ __global__ void __launch_bounds__(FT_NT, 2) k_mg_post_fused(Dom D, float* __rest
         // last half-sweep on plane t-4 (colour 0, the tile only); each thread then stores its quad and
         // adds r z of its four cells to the product
         const int tf = t - 4;
+        // every lane takes part (the half-sweep votes across the warp); with halo 0 only the tile's
+        // cells in the domain change
+        if (tf >= k0 && tf < k1) ft_half_sweep(D, S, P, Q, R, 4, tf, 0, 0, scale, 4);
         if (tf >= k0 && tf < k1 && Q.tile >= 0 && Q.dom == 0xfu) {
-            ft_half_sweep(D, S, P, Q, R, 4, tf, 0, 0, scale, 4);
             const int s = R.sl[4];
             const float4 z4 = lds4(S.z(s) + Q.c), r4 = lds4(S.r(s) + Q.c);
             *reinterpret_cast<float4*>(z + Q.gx + (long long)D.sy * Q.gy + D.sz * tf) = z4;
