@@ -127,6 +127,12 @@ __device__ __forceinline__ bool fast_cell(const Dom& D, long long P, int i, int 
 // cell across that face alone), so cells on the domain faces are fast too.  Links through a domain
 // face take the boundary forms of flux_general (near-cell nu_t and cross derivative, central advected
 // value).  Cells that are not fast_cell are skipped (the general kernel takes them).
+//
+// The flux form is conservative: the face between L and R = L + e_a gives L the term Phi and R the
+// term -Phi, so the march evaluates every face once.  Each thread takes its cell's -x, -y and +z
+// faces (two warps add the tile's last x column and y row); the x and y faces meet in shared memory,
+// the z face stays in registers for the next plane.  A plane's sums run one step later, so a single
+// barrier per plane orders both the face buffers (two of them, by plane parity) and the ring.
 #define FT_X 32
 #define FT_Y 8
 #define FT_H 2
@@ -136,6 +142,8 @@ __device__ __forceinline__ bool fast_cell(const Dom& D, long long P, int i, int 
 #define FT_NV 4
 #define FT_KZ 16
 #define FT_RING 6
+#define FT_FXN (FT_Y * (FT_X + 1))   // x faces of a tile plane, per component
+#define FT_FYN ((FT_Y + 1) * FT_X)   // y faces
 
 // Domain-boundary ghost of component c across face (a, s) of the cell holding v (vel_across's rules).
 template <class T>
@@ -145,6 +153,53 @@ __device__ __forceinline__ T bc_ghost(const Dom& D, int a, int s, int c, T v) {
         case IBM_BC_OUTFLOW: return v;
         case IBM_BC_SLIP: return c == a ? -v : v;
         default: return -v;
+    }
+}
+
+// Phi of the face between L = R - e_A and R, per component: the term of L's flux sum (R takes -Phi).
+// S[d] is ring plane k + d - 2; R sits at in-plane ring index c0 of plane k + ZR and at global (g0, g1,
+// g2), g_A = 0 .. n_A naming the face.  A face on a non-periodic domain side (R or L outside) takes the
+// boundary forms of the cell inside.  Positions outside the domain give unused values (U reads 0).
+template <class T, int A, int ZR>
+__device__ __forceinline__ void ft_face(const Dom& D, const FaceLayout& F, const T* __restrict__ U,
+                                        const T* const (&S)[5], int c0, int g0, int g1, int g2, T nu, T gam,
+                                        T inv2dx, T invdx, T (&phi)[3]) {
+    constexpr int EX = A == 0, EY = A == 1, EZ = A == 2;
+    // variable v at R + (dx, dy, dz)
+    auto V = [&](int v, int dx, int dy, int dz) -> T { return S[ZR + 2 + dz][v * FT_PL + c0 + dy * FT_SX + dx]; };
+    const int g[3] = {g0, g1, g2}, n[3] = {D.nx, D.ny, D.nz};
+    const bool per = D.bc[2 * A] == IBM_BC_PERIODIC;
+    const bool dlo = !per && g[A] == 0, dhi = !per && g[A] == n[A];
+    bool valid = g[A] >= 0 && g[A] <= n[A];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        if (b != A) valid = valid && g[b] >= 0 && g[b] < n[b];
+    const T Uf = valid ? U[F.index(A, g0, g1, g2)] : (T)0;
+    const T nutL = V(3, -EX, -EY, -EZ), nutR = V(3, 0, 0, 0);
+    const T nutf = dlo ? nutR : (dhi ? nutL : (T)0.5 * (nutL + nutR));
+    const T nuf = nu + nutf;
+    const bool quick = gam != (T)0 && !dlo && !dhi;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T uL = V(c, -EX, -EY, -EZ), uR = V(c, 0, 0, 0);
+        const T D1 = (uR - uL) * invdx;
+        T Tt = D1;
+        if (c != A) {
+            // d u_A / d x_c at L and at R (central)
+            const int cx = c == 0, cy = c == 1, cz = c == 2;
+            const T gL = (V(A, cx - EX, cy - EY, cz - EZ) - V(A, -cx - EX, -cy - EY, -cz - EZ)) * inv2dx;
+            const T gR = (V(A, cx, cy, cz) - V(A, -cx, -cy, -cz)) * inv2dx;
+            Tt = dlo ? gR : (dhi ? gL : (T)0.5 * (gL + gR));
+        }
+        T adv = (T)0.5 * (uL + uR);
+        if (quick) {
+            // far upwind: L - e_A for U >= 0, R + e_A otherwise
+            const bool up = Uf >= (T)0;
+            const T far = up ? V(c, -2 * EX, -2 * EY, -2 * EZ) : V(c, EX, EY, EZ);
+            const T q = up ? ((T)6 * uL + (T)3 * uR - far) / (T)8 : ((T)6 * uR + (T)3 * uL - far) / (T)8;
+            adv = ((T)1 - gam) * adv + gam * q;
+        }
+        phi[c] = -Uf * adv + nuf * D1 + nutf * Tt;
     }
 }
 
@@ -212,6 +267,8 @@ __device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& 
         }
     };
     const int cidx = (ty + FT_H) * FT_SX + (tx + FT_H);
+    T* const fxs = sm + FT_RING * FT_NV * FT_PL;     // [parity][component][FT_Y][FT_X + 1]
+    T* const fys = fxs + 2 * 3 * FT_FXN;               // [parity][component][FT_Y + 1][FT_X]
     for (long long item = blockIdx.x; item < items; item += gridDim.x) {
         x0 = (int)(item % gx) * FT_X;
         y0 = (int)((item / gx) % gy) * FT_Y;
@@ -221,86 +278,91 @@ __device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& 
             fetch(kk);
             commit(kk);
         }
+        if (z0 + 3 <= z1 + 1) fetch(z0 + 3);
         __syncthreads();
         const int i = x0 + tx, j = y0 + ty;
-        for (int k = z0; k < z1; ++k) {
-            // plane k + 3 is fetched while plane k is computed and lands in the ring slot that plane
-            // k - 3 left; the barrier at the end of the step publishes it
-            const bool more = k + 3 <= z1 + 1;
-            if (more) fetch(k + 3);
-            const long long P = i + (long long)D.sy * j + D.sz * k;
-            if (i < D.nx && j < D.ny && (D.fast ? D.fast[P] != 0 : fast_cell(D, P, i, j, k))) {
-                const int xc[3] = {i, j, k};
-                const T* S[5];
+        const bool inxy = i < D.nx && j < D.ny;
+        // the cell of the plane whose sums are pending: fast, index, u; its -z and +z faces
+        bool pf_fast = false;
+        long long pP = 0;
+        T pu[3] = {0, 0, 0}, zlo[3] = {0, 0, 0}, zhi[3] = {0, 0, 0};
+        int s0 = slot(z0 - 2);          // ring slot of plane k - 2, advanced with k (no division per cell)
+        for (int k = z0; k <= z1; ++k, s0 = s0 + 1 == FT_RING ? 0 : s0 + 1) {
+            // plane k + 3, fetched into registers during the previous step, goes into the ring slot that
+            // plane k - 3 left (the previous barrier ended every read of it); then plane k + 4 is fetched,
+            // so each load has a whole step and a barrier to land.  The barrier at the end of the step
+            // publishes plane k + 3.
+            if (k < z1 && k + 3 <= z1 + 1) {
+                T* dst = sm + (s0 == 0 ? FT_RING - 1 : s0 - 1) * (FT_NV * FT_PL);   // slot of k - 3 = s0 - 1
 #pragma unroll
-                for (int d = 0; d < 5; ++d) S[d] = sm + slot(k + d - 2) * (FT_NV * FT_PL) + cidx;
-                // value of variable v at (i + dx, j + dy, k + dz)
-                auto V = [&](int v, int dx, int dy, int dz) -> T { return S[dz + 2][v * FT_PL + dy * FT_SX + dx]; };
-                const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-                const T nutP = V(3, 0, 0, 0);
-                T h[3] = {0, 0, 0};
-                T uc[3], un[3][6], GP[3][3];
+                for (int t = 0; t < 2; ++t) {
+                    const int e = tid + t * (FT_X * FT_Y);
+                    if (e >= FT_PL) continue;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uc[c] = V(c, 0, 0, 0);
+                    for (int v = 0; v < FT_NV; ++v) dst[v * FT_PL + e] = pf[t][v];
+                }
+                if (k + 4 <= z1 + 1) fetch(k + 4);
+            }
+            if (k > z0) {
+                // sums of plane k - 1, whose faces the previous step wrote
+                if (pf_fast) {
+                    const int pb = (k - 1) & 1;
+                    const T* fx = fxs + pb * 3 * FT_FXN + ty * (FT_X + 1) + tx;
+                    const T* fy = fys + pb * 3 * FT_FYN + ty * FT_X + tx;
+                    T h[3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        un[c][2 * a] = V(c, -e[a][0], -e[a][1], -e[a][2]);
-                        un[c][2 * a + 1] = V(c, e[a][0], e[a][1], e[a][2]);
-                    }
+                    for (int c = 0; c < 3; ++c)
+                        h[c] = ((fx[c * FT_FXN + 1] - fx[c * FT_FXN]) + (fy[c * FT_FYN + FT_X] - fy[c * FT_FYN]) +
+                                (zhi[c] - zlo[c])) * invdx;
+                    epi(pP, h, pu);
                 }
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) GP[a][b] = (un[b][2 * a + 1] - un[b][2 * a]) * inv2dx;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int s = -1; s <= 1; s += 2) {
-                        const int lb = 2 * a + (s > 0);
-                        const T Uf = U[F.index(a, i + (a == 0 && s > 0), j + (a == 1 && s > 0), k + (a == 2 && s > 0))];
-                        const int ox = s * e[a][0], oy = s * e[a][1], oz = s * e[a][2];
-                        // a link through a non-periodic domain face
-                        const bool dom = (xc[a] + s < 0 || xc[a] + s >= n[a]) && D.bc[2 * a] != IBM_BC_PERIODIC;
-                        const T nutf = dom ? nutP : (T)0.5 * (nutP + V(3, ox, oy, oz));
-                        T GN[3] = {0, 0, 0};
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            if (q == a) continue;
-                            GN[q] = (V(a, ox + e[q][0], oy + e[q][1], oz + e[q][2]) -
-                                     V(a, ox - e[q][0], oy - e[q][1], oz - e[q][2])) * inv2dx;
-                        }
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const T uP = uc[c], uN = un[c][lb];
-                            const T D1 = (uN - uP) * invdx;
-                            const T Tt = c == a ? D1 : (dom ? (T)s * GP[c][a] : (T)s * (T)0.5 * (GP[c][a] + GN[c]));
-                            T adv = (T)0.5 * (uP + uN);
-                            if (gam != (T)0 && !dom) {
-                                // far upwind: L - e_a for U >= 0 (L = P or P - e_a), R + e_a otherwise
-                                const T uL = s > 0 ? uP : uN, uR = s > 0 ? uN : uP;
-                                const int fo = Uf >= (T)0 ? (s > 0 ? -1 : -2) : (s > 0 ? 2 : 1);
-                                const T far = V(c, fo * e[a][0], fo * e[a][1], fo * e[a][2]);
-                                const T q = Uf >= (T)0 ? ((T)6 * uL + (T)3 * uR - far) / (T)8
-                                                       : ((T)6 * uR + (T)3 * uL - far) / (T)8;
-                                adv = ((T)1 - gam) * adv + gam * q;
-                            }
-                            const T conv = -(T)s * Uf * adv;
-                            h[c] += conv + (nu + nutf) * D1 + nutf * Tt;
-                        }
-                    }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] *= invdx;
-                epi(P, h, uc);
+                for (int c = 0; c < 3; ++c) zlo[c] = zhi[c];
             }
-            if (more) commit(k + 3);
+            if (k == z1) break;
+            const T* S[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+                const int sd = s0 + d;
+                S[d] = sm + (sd >= FT_RING ? sd - FT_RING : sd) * (FT_NV * FT_PL);
+            }
+            const long long P = i + (long long)D.sy * j + D.sz * k;
+            pf_fast = inxy && (D.fast ? D.fast[P] != 0 : fast_cell(D, P, i, j, k));
+            pP = P;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pu[c] = S[2][c * FT_PL + cidx];
+            if (k == z0) ft_face<T, 2, 0>(D, F, U, S, cidx, i, j, k, nu, gam, inv2dx, invdx, zlo);
+            ft_face<T, 2, 1>(D, F, U, S, cidx, i, j, k + 1, nu, gam, inv2dx, invdx, zhi);
+            const int b = k & 1;
+            T* fx = fxs + b * 3 * FT_FXN;
+            T* fy = fys + b * 3 * FT_FYN;
+            T ph[3];
+            ft_face<T, 0, 0>(D, F, U, S, cidx, i, j, k, nu, gam, inv2dx, invdx, ph);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fx[c * FT_FXN + ty * (FT_X + 1) + tx] = ph[c];
+            ft_face<T, 1, 0>(D, F, U, S, cidx, i, j, k, nu, gam, inv2dx, invdx, ph);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fy[c * FT_FYN + ty * FT_X + tx] = ph[c];
+            if (ty == 0) {
+                // the +y faces of the tile's last row
+                ft_face<T, 1, 0>(D, F, U, S, (FT_Y + FT_H) * FT_SX + tx + FT_H, i, y0 + FT_Y, k, nu, gam, inv2dx,
+                                 invdx, ph);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fy[c * FT_FYN + FT_Y * FT_X + tx] = ph[c];
+            } else if (ty == 1 && tx < FT_Y) {
+                // the +x faces of the tile's last column (row tx)
+                ft_face<T, 0, 0>(D, F, U, S, (tx + FT_H) * FT_SX + FT_X + FT_H, x0 + FT_X, y0 + tx, k, nu, gam,
+                                 inv2dx, invdx, ph);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fx[c * FT_FXN + tx * (FT_X + 1) + FT_X] = ph[c];
+            }
             __syncthreads();
         }
     }
 }
 
 template <class T>
-size_t fast_tile_smem() { return (size_t)FT_RING * FT_NV * FT_PL * sizeof(T); }
+size_t fast_tile_smem() { return (size_t)(FT_RING * FT_NV * FT_PL + 2 * 3 * (FT_FXN + FT_FYN)) * sizeof(T); }
 
 template <class T>
 __device__ __forceinline__ void flux_general(const Dom& D, const FaceLayout& F, const T* __restrict__ u,
@@ -1061,11 +1123,14 @@ __global__ void k_row_scan(long long nrows, unsigned long long* __restrict__ rc,
 }  // namespace
 
 int flux_kernels_setup() {
-    // the FP64 tiles need more than the default 48 KB of dynamic shared memory
-    const int bytes = (int)fast_tile_smem<double>();
+    // the tiles need more than the default 48 KB of dynamic shared memory
+    const int bytes = (int)fast_tile_smem<double>(), bytesf = (int)fast_tile_smem<float>();
     IBM_CUDA(cudaFuncSetAttribute(k_predict<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     IBM_CUDA(cudaFuncSetAttribute(k_cn_begin<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     IBM_CUDA(cudaFuncSetAttribute(k_cn_apply<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    IBM_CUDA(cudaFuncSetAttribute(k_predict<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytesf));
+    IBM_CUDA(cudaFuncSetAttribute(k_cn_begin<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytesf));
+    IBM_CUDA(cudaFuncSetAttribute(k_cn_apply<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytesf));
     int dev = 0, nsm = IBM_NSM, bf = 0, bd = 0;
     IBM_CUDA(cudaGetDevice(&dev));
     IBM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
