@@ -784,7 +784,7 @@ def main():
     ap.add_argument("--quick", type=float, default=0.1, help="QUICK fraction of the advected face value")
     ap.add_argument("--mg-sweeps", type=int, default=2, help="red-black sweeps before and after each coarse correction")
     ap.add_argument("--mg-omega", type=float, default=1.6, help="multigrid coarse-correction factor")
-    ap.add_argument("--inner-tol", type=float, default=1e-4,
+    ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="FP32 inner solve: residual reduction per FP64 refinement")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -218,7 +218,27 @@ __device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& 
     // the planes' values a thread stages: FT_PL <= 2 * 256 halo-tile positions per plane
     T pf[2][FT_NV];
     int x0 = 0, y0 = 0;
+    // the thread's halo-tile positions (fixed) and whether the tile's halo box lies inside the domain
+    // in x and y (then a plane inside the domain needs no boundary logic)
+    const int ex0 = tid % FT_SX - FT_H, ey0 = tid / FT_SX - FT_H;
+    const int ex1 = (tid + FT_X * FT_Y) % FT_SX - FT_H, ey1 = (tid + FT_X * FT_Y) / FT_SX - FT_H;
+    bool inner = false;
     auto fetch = [&](int kk) {
+        if (inner && kk >= 0 && kk < D.nz) {
+            const long long base = x0 + (long long)D.sy * y0 + D.sz * kk;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int e = tid + t * (FT_X * FT_Y);
+                pf[t][0] = pf[t][1] = pf[t][2] = pf[t][3] = (T)0;
+                if (e >= FT_PL) continue;
+                const long long c = base + (t ? ex1 : ex0) + (long long)D.sy * (t ? ey1 : ey0);
+                pf[t][0] = u[c];
+                pf[t][1] = u[D.N + c];
+                pf[t][2] = u[2 * D.N + c];
+                pf[t][3] = nut[c];
+            }
+            return;
+        }
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int e = tid + t * (FT_X * FT_Y);
@@ -272,6 +292,7 @@ __device__ __forceinline__ void fast_tile_march(const Dom& D, const FaceLayout& 
     for (long long item = blockIdx.x; item < items; item += gridDim.x) {
         x0 = (int)(item % gx) * FT_X;
         y0 = (int)((item / gx) % gy) * FT_Y;
+        inner = x0 >= FT_H && x0 + FT_X + FT_H <= D.nx && y0 >= FT_H && y0 + FT_Y + FT_H <= D.ny;
         const int z0 = (int)(item / ((long long)gx * gy)) * FT_KZ;
         const int z1 = z0 + FT_KZ < D.nz ? z0 + FT_KZ : D.nz;
         for (int kk = z0 - 2; kk <= z0 + 2; ++kk) {

@@ -489,6 +489,7 @@ int pcg_cycles(const LesCtx& c, PoissonWork& w, T* x, int check_every, cudaStrea
         if (rc) return rc;
     }
     const int pairs = (check_every + 1) / 2;
+    double rr_last = -1.0;
     for (int m = 0;;) {
         if (graphs) {
             for (int q = 0; q < pairs; ++q) IBM_CUDA(cudaGraphLaunch(w.gexec, s));
@@ -503,6 +504,11 @@ int pcg_cycles(const LesCtx& c, PoissonWork& w, T* x, int check_every, cudaStrea
         int rc = read_scalars(w, s);
         if (rc) return rc;
         if (w.hsc->done) return IBM_OK;
+        // an inner solve that has stopped converging (at the floor of its working precision) hands back
+        // to the refinement: less than a factor 2 of residual norm over a whole check interval
+        const double rr = w.hsc->rr;
+        if (rr_last > 0.0 && rr > 0.25 * rr_last) return IBM_OK;
+        rr_last = rr;
     }
 }
 

@@ -4,7 +4,7 @@ the FP64 CPU oracle.
 Workloads: the 512x256x256 cube and plate on a no-slip floor, and the 1024x512x384 vehicle-like
 assembly (about 2 M dirty triangles, gaps, nested parts, dead-end filter on).  Scheme: FP32 stencils
 with FP64 iterative refinement, Crank-Nicolson with 10 % QUICK, CG preconditioned by the connected-part
-multigrid with omega 1.6, inner tolerance 1e-4 and residual checks every 8 iterations.  After a few
+multigrid with omega 1.6, inner tolerance 1e-5 and residual checks every 8 iterations.  After a few
 steps on the GPU:
 - every operator of the step, applied by the GPU to its own full-size fields, matches the oracle on a
   z-slab: the oracle runs on the slab plus two planes each side (the stencils reach two cells) and the
@@ -42,7 +42,7 @@ def L():
 
 def bench_solver(L, g, cfg, geo, tol=None):
     return L.Solver(g, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, precision=L.FP32_REFINE64, solver=L.CG,
-                    tol=cfg.tol if tol is None else tol, check_every=8, inner_tol=1e-4, geometry=geo,
+                    tol=cfg.tol if tol is None else tol, check_every=8, inner_tol=1e-5, geometry=geo,
                     precond=L.MULTIGRID, mg_sweeps=2, mg_omega=1.6, quick=QUICK, integrator=L.CRANK_NICOLSON)
 
 
