@@ -486,6 +486,7 @@ def measure(L, torch, name, args, world, stream, precision=None, steps=None, war
            "steps": steps, "warmup": warmup, "timed_steps": [warmup + 1, warmup + steps], "gpu_launches": launches,
            "solve": solve_summary(stats), "clocks": clk}
     s_bytes = 8 if solver.params.precision == L.FP64 else 4
+    out["precision"] = "fp32" if s_bytes == 4 else "fp64"
     if profile:
         peak, peak_kind = read_peaks()
         prof, groups = kernel_groups(solver, torch, st, steps, N, s_bytes, args, tol, peak)
@@ -627,10 +628,24 @@ def roofline_of(m, workload):
     g = groups[dom]
     peak, kind = m["peak"]
     names = dict(GROUP_KERNEL, **(GROUP_KERNEL_FUSED if m.get("mg", {}).get("fused_fine_passes") else {}))
+    # the whole step against HBM: the groups' algorithmic bytes per step (the coarse multigrid levels and
+    # the forcing have no byte model and are left out), and the plain-CG byte model of the method,
+    # 119 + 41 I + 41 R bytes per cell in FP32 + refinement, 235 + 81 I in FP64 (I inner iterations,
+    # R refinements per step)
+    alg = sum(v["bytes_per_launch"] * v["launches"] for v in m["groups"].values()) / m["steps"]
+    sv = m["solve"]
+    fp32 = m.get("precision", "fp32") == "fp32"
+    model = (119 + 41 * sv["inner_iters_per_step"] + 41 * sv["refinements_per_step"] if fp32
+             else 235 + 81 * sv["inner_iters_per_step"]) * m["cells"]
+    sec = m["ms_per_step"] * 1e-3
+    step = {"algorithmic_bytes_per_step": alg, "achieved": alg / sec / 1e9, "frac": alg / sec / 1e9 / peak,
+            "cg_model_bytes_per_step": model, "cg_model_frac": model / sec / 1e9 / peak,
+            "note": "whole step: all groups' algorithmic bytes / the timed step; cg_model is the plain-CG "
+                    "byte model (no preconditioner, explicit momentum) at the measured iteration counts"}
     return {"bound": "hbm", "kernel": dom, "kernel_name": names.get(dom, dom), "mg": m.get("mg"),
             "achieved": g["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": g["achieved_gbs"] / peak,
             "traffic": ncu_traffic(dom, workload), "algorithmic_bytes_per_launch": g["bytes_per_launch"],
-            "avg_launch_ms": g["avg_launch_ms"], "peak_source": kind, "shares": m["shares"],
+            "avg_launch_ms": g["avg_launch_ms"], "peak_source": kind, "step": step, "shares": m["shares"],
             "groups": m["groups"],
             "note": "kernel times from a second pass of the same number of steps with per-kernel events on the "
                     "launching stream (graphs off); frac is of the measured copy peak"}
