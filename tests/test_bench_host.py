@@ -1,5 +1,6 @@
-"""Host logic of bench.py that needs no GPU: the clock record taken during the timed region and the
-guard that drops the ncu traffic figure once the kernel's sources change."""
+"""Host logic of bench.py that needs no GPU: the clock record taken during the timed region, the
+guard that drops the ncu traffic figure once the kernel's sources change, and the roofline object
+(the dominant group and the whole-step byte sums)."""
 import json
 import os
 
@@ -66,3 +67,38 @@ def test_source_hash_covers_only_the_named_files():
     assert bench.src_hash(rec_files) != bench.src_hash(rec_files[:2])
     with pytest.raises(FileNotFoundError):
         bench.src_hash(["no_such_file.cu"])
+
+
+def _measurement(precision="fp32"):
+    """A made-up measurement: two kernel groups and the momentum solve over 20 steps."""
+    groups = {
+        "mg_fine": {"launches": 700, "launches_incl_empty": 960, "avg_launch_ms": 3.3, "bytes_per_launch": 2.2e9,
+                    "achieved_gbs": 2.2e9 / 3.3e-3 / 1e9, "frac": 0.1},
+        "cg_update": {"launches": 350, "launches_incl_empty": 480, "avg_launch_ms": 0.75, "bytes_per_launch": 4.8e9,
+                      "achieved_gbs": 4.8e9 / 0.75e-3 / 1e9, "frac": 0.94},
+        "momentum_per_step": {"launches": 20, "avg_launch_ms": 120.0, "bytes_per_launch": 2.3e11,
+                              "achieved_gbs": 2.3e11 / 0.12 / 1e9, "frac": 0.28},
+    }
+    return {"groups": groups, "peak": (6784.5, "measured"), "steps": 20, "cells": 201326592, "ms_per_step": 363.4,
+            "precision": precision, "shares": {}, "solve": {"inner_iters_per_step": 17.2, "refinements_per_step": 1.0}}
+
+
+def test_roofline_takes_the_group_with_the_largest_total_time_and_sums_the_step():
+    m = _measurement()
+    r = bench.roofline_of(m, "no_such_workload")
+    # mg_fine: 700 x 3.3 ms > cg_update: 350 x 0.75 ms; the momentum solve is a per-step group, not a kernel
+    assert r["kernel"] == "mg_fine"
+    assert r["frac"] == pytest.approx(2.2e9 / 3.3e-3 / 1e9 / 6784.5)
+    assert r["traffic"] is None
+    step = r["step"]
+    alg = (700 * 2.2e9 + 350 * 4.8e9 + 20 * 2.3e11) / 20
+    assert step["algorithmic_bytes_per_step"] == pytest.approx(alg)
+    assert step["frac"] == pytest.approx(alg / 0.3634 / 1e9 / 6784.5)
+    model = (119 + 41 * 17.2 + 41 * 1.0) * 201326592
+    assert step["cg_model_bytes_per_step"] == pytest.approx(model)
+    assert step["cg_model_frac"] == pytest.approx(model / 0.3634 / 1e9 / 6784.5)
+
+
+def test_step_model_of_the_fp64_path():
+    r = bench.roofline_of(_measurement("fp64"), "no_such_workload")
+    assert r["step"]["cg_model_bytes_per_step"] == pytest.approx((235 + 81 * 17.2) * 201326592)
