@@ -507,10 +507,13 @@ def measure(L, torch, name, args, world, stream, precision=None, steps=None, war
                                            "frac": mb / (mms * 1e-3) / 1e9 / peak}
     if e2e_steps:
         # end to end through the public entry point with host buffers: H2D of the step's state from
-        # pinned memory, the step, D2H of its result, every step; each step's status is checked
+        # pinned memory, the step, D2H of its result, every step; each step's status is checked.  The
+        # state is u, U and p (p^n is the pressure solve's initial guess); H = L(u^n) is an input only
+        # of the Adams-Bashforth step (Crank-Nicolson recomputes it), so it travels only then.
         ke = min(steps, e2e_steps)
-        host = {k: st[k].cpu().pin_memory() for k in ("u", "U", "p", "H")}
-        dev = {k: torch.empty_like(st[k]) for k in host}
+        keys = ("u", "U", "p", "H") if solver.params.integrator == L.ADAMS_BASHFORTH else ("u", "U", "p")
+        host = {k: st[k].cpu().pin_memory() for k in keys}
+        dev = {k: torch.empty_like(st[k]) for k in ("u", "U", "p", "H")}
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         stats = L.Stats()
         torch.cuda.synchronize()
