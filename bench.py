@@ -41,7 +41,7 @@ UNIT = "Mcell-steps/s"
 FALLBACK_HBM = 6800.0
 # CG iterations per step charged to the oracle's sample step (about the GPU's measured mean of
 # multigrid-preconditioned CG on the vehicle workload; the sample runs exactly this many)
-I_REF_DEFAULT = 30
+I_REF_DEFAULT = 18
 
 
 def bytes_per_cell(s, integrator="cn", sweeps=2, fused=False):
@@ -213,14 +213,26 @@ def workload_config(name, args, precision="fp32"):
 # ------------------------------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, on bounded samples of the same workload
 
-def _slab_case(cfg, planes, k0, quick):
+def slab_shape(cfg):
+    """Planes and rows of the oracle's sample of a workload: the largest workload takes one plane and the
+    middle quarter of the rows (through the bodies), so that a sample step lasts a few seconds; the others
+    take two whole planes."""
+    if cfg.ncell > 50_000_000:
+        return 1, cfg.ny // 4
+    return 2, cfg.ny
+
+
+def _slab_case(cfg, planes, k0, quick, rows=None):
     import oracle
+    rows = cfg.ny if rows is None else rows
+    j0 = (cfg.ny - rows) // 2
     tri = cfg.soup().copy()
     tri[..., 2] -= k0
-    case = oracle.Case(cfg.nx, cfg.ny, planes, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
+    tri[..., 1] -= j0
+    case = oracle.Case(cfg.nx, rows, planes, cfg.dx, cfg.nu, cfg.dt, cfg.bc, cfg.u_in, cfg.csm_on,
                        cfg.forcing_on, cfg.deadend_on, quick)
     case.set_geometry(tri)
-    u = W.initial_fields(W.Config("slab", cfg.nx, cfg.ny, planes, 0, 0, 0, 0, 0, cfg.bc, seed=cfg.seed)).reshape(-1)
+    u = W.initial_fields(W.Config("slab", cfg.nx, rows, planes, 0, 0, 0, 0, 0, cfg.bc, seed=cfg.seed)).reshape(-1)
     return case, u
 
 
@@ -238,10 +250,10 @@ class OracleSample:
     solve, correction -- the per-cell work of a full step.  The slab is classified once; every step()
     starts from the same initial field and times the step alone."""
 
-    def __init__(self, name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6):
+    def __init__(self, name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6, rows=None):
         cfg = W.get_config(name)
         self.k0 = slab_k0(cfg, planes) if k0 is None else k0
-        self.case, self.u = _slab_case(cfg, planes, self.k0, quick)
+        self.case, self.u = _slab_case(cfg, planes, self.k0, quick, rows)
         self.iters, self.integrator, self.mom_tol, self.planes = int(iters), integrator, mom_tol, planes
 
     def step(self):
@@ -263,13 +275,13 @@ class OracleSample:
         return {"cells": case.N, "seconds": t1 - t0, "k0": self.k0, "planes": self.planes, "cg_iters": st.iters}
 
 
-def oracle_sample_step(name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6):
-    return OracleSample(name, iters, planes, k0, integrator, quick, mom_tol).step()
+def oracle_sample_step(name, iters, planes, k0=None, integrator="cn", quick=0.1, mom_tol=1e-6, rows=None):
+    return OracleSample(name, iters, planes, k0, integrator, quick, mom_tol, rows).step()
 
 
 def _sample_worker(args):
-    name, iters, planes, k0, integrator, quick = args
-    return oracle_sample_step(name, iters, planes, k0, integrator, quick)
+    name, iters, planes, k0, integrator, quick, rows = args
+    return oracle_sample_step(name, iters, planes, k0, integrator, quick, rows=rows)
 
 
 def oracle_full_run(name):
@@ -290,13 +302,14 @@ def _full_run_worker(name):
     return oracle_full_run(name)
 
 
-def _sample_desc(name, planes, iters, integrator):
+def _sample_desc(name, planes, iters, integrator, rows=None):
     cfg = W.get_config(name)
-    return ("oracle (FP64, plain C) step on a %dx%dx%d z-slab of %s: csm, %s predictor, forcing, faces, rhs, "
-            "%d CG iterations (about the GPU's multigrid-preconditioned count per step), correction; value = "
-            "slab cells / seconds of that step" % (cfg.nx, cfg.ny, planes, name,
-                                                   "Crank-Nicolson (momentum BiCGStab to 1e-6)" if integrator == "cn"
-                                                   else "AB2", iters))
+    rows = cfg.ny if rows is None else rows
+    return ("oracle (FP64, plain C) step on a %dx%dx%d slab of %s (the middle %d of %d rows, %d plane%s through "
+            "the bodies): csm, %s predictor, forcing, faces, rhs, %d CG iterations (about the GPU's "
+            "multigrid-preconditioned count per step), correction; value = slab cells / seconds of that step"
+            % (cfg.nx, rows, planes, name, rows, cfg.ny, planes, "" if planes == 1 else "s",
+               "Crank-Nicolson (momentum BiCGStab to 1e-6)" if integrator == "cn" else "AB2", iters))
 
 
 def run_reference(args):
@@ -304,8 +317,8 @@ def run_reference(args):
     if rank != 0:
         return
     I = int(os.environ.get("IBM_REF_ITERS", I_REF_DEFAULT))
-    planes = 1 if W.get_config(args.workload).ncell > 50_000_000 else 2
-    sample = OracleSample(args.workload, I, planes, integrator=args.integrator, quick=args.quick)
+    planes, rows = slab_shape(W.get_config(args.workload))
+    sample = OracleSample(args.workload, I, planes, integrator=args.integrator, quick=args.quick, rows=rows)
     for _ in range(args.warmup):
         sample.step()
     samples = [sample.step() for _ in range(args.steps)]
@@ -318,7 +331,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": _sample_desc(args.workload, planes, I, args.integrator),
+                             "sample": _sample_desc(args.workload, planes, I, args.integrator, rows),
                              "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -660,21 +673,21 @@ def cpu_baseline(args, iters, pool_result):
     import multiprocessing as mp
     name = args.workload
     cfg = W.get_config(name)
-    planes = 1 if cfg.ncell > 50_000_000 else 2
-    one = oracle_sample_step(name, iters, planes, integrator=args.integrator, quick=args.quick)
+    planes, rows = slab_shape(cfg)
+    one = oracle_sample_step(name, iters, planes, integrator=args.integrator, quick=args.quick, rows=rows)
     ncores = os.cpu_count() or 1
     k0s = [int(v) for v in np.linspace(0, cfg.nz // 2 - planes, ncores)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(ncores) as pool:
         t0 = time.perf_counter()
-        res = pool.map(_sample_worker, [(name, iters, planes, k, args.integrator, args.quick) for k in k0s])
+        res = pool.map(_sample_worker, [(name, iters, planes, k, args.integrator, args.quick, rows) for k in k0s])
         wall = time.perf_counter() - t0
     all_cells = sum(r["cells"] for r in res)
     # the slab-steps' own compute time (processes start and classify before they time)
     slowest = max(r["seconds"] for r in res)
     full = pool_result.get() if pool_result is not None else None
     out = {"value": one["cells"] / one["seconds"] / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": _sample_desc(name, planes, iters, args.integrator),
+           "sample": _sample_desc(name, planes, iters, args.integrator, rows),
            "host_cores": ncores,
            "all_cores": {"value": all_cells / slowest / 1e6, "cores": ncores, "wall_s_incl_setup": wall,
                          "note": "%d processes, each one slab step of the same workload at a different height, "
