@@ -587,7 +587,7 @@ def train_guess(L, torch, args):
     for epoch in range(args.learn_epochs):
         for (b, p_n, p_p, p_next) in snaps:
             _, sc = net.forward(g, b, p_n, p_p, geo.flags)
-            target = ((p_next - 2.0 * p_n + p_p) / sc).to(torch.float32)
+            target = net.target(g, p_next, p_n, p_p, sc)
             losses.append(net.train_step(g, b, p_n, p_p, target, args.learn_lr, geo.flags))
     torch.cuda.synchronize()
     t_train = time.time() - t0

@@ -298,8 +298,13 @@ int ibm_net_get_grads(const ibm_net* net, float* h_grads);
  * synchronises) = s.  d_flags may be NULL (no body). */
 int ibm_net_forward(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
                     const double* d_pprev, const uint8_t* d_flags, float* d_out, double* scale, void* stream);
+/* The training target of a snapshot: d_target[N] (float) = (p^{n+1} - 2 p^n + p^{n-1}) / s, formed in
+ * FP64 on the device; s > 0 is the scale ibm_net_forward returned for (b, p^n, p^{n-1}).  All arrays are
+ * device arrays of N = nx ny nz values owned by the caller.  IBM_E_INVALID on a null array or s <= 0. */
+int ibm_net_target(const ibm_grid* grid, const double* d_pnext, const double* d_p, const double* d_pprev,
+                   double s, float* d_target, void* stream);
 /* One Adam step (betas 0.9, 0.999) on the mean squared error against
- * d_target[N] = (p^{n+1} - 2 p^n + p^{n-1}) / s;
+ * d_target[N] = (p^{n+1} - 2 p^n + p^{n-1}) / s (ibm_net_target);
  * lr = 0 only computes the gradients.  *loss (host, synchronises) = the loss before the update. */
 int ibm_net_train_step(ibm_net* net, const ibm_grid* grid, const double* d_b, const double* d_p,
                        const double* d_pprev, const uint8_t* d_flags, const float* d_target, float lr,

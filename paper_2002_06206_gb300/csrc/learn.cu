@@ -336,6 +336,13 @@ long long offset_w(int l) { return l == 0 ? 0 : (l == 1 ? NN_C * NN_TAPS * NN_C 
 long long offset_b(int l) { return 2 * NN_C * NN_TAPS * NN_C + NN_TAPS * NN_C + l * NN_C; }
 int cout_of(int l) { return l == 2 ? 1 : NN_C; }
 
+// The training target of a snapshot, (p^{n+1} - 2 p^n + p^{n-1}) / s, formed in FP64 and stored in FP32.
+__global__ void k_net_target(long long N, const double* __restrict__ pnext, const double* __restrict__ p,
+                             const double* __restrict__ pprev, double s, float* __restrict__ out) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x)
+        out[q] = (float)((pnext[q] - 2.0 * p[q] + pprev[q]) / s);
+}
+
 }  // namespace
 
 // ---- host side -----------------------------------------------------------------------------------
@@ -483,9 +490,24 @@ extern "C" int ibm_net_forward(ibm_net* n, const ibm_grid* g, const double* d_b,
     return IBM_OK;
 }
 
-// One training step on a snapshot: features from (b, p, p_prev, flags), target = (p_next - p) / s,
-// forward, mean squared error, backward, Adam (lr; betas 0.9, 0.999).  *loss (host, synchronises) =
-// the mean squared error before the update.  lr = 0 computes the gradients only.
+// The training target of a snapshot: d_target[N] = (p_next - 2 p + p_prev) / s in FP32, s the scale that
+// ibm_net_forward returned for (b, p, p_prev).
+extern "C" int ibm_net_target(const ibm_grid* g, const double* d_pnext, const double* d_p, const double* d_pprev,
+                              double s, float* d_target, void* stream) {
+    int rc = ibm_check_grid(g);
+    if (rc) return rc;
+    if (!d_pnext || !d_p || !d_pprev || !d_target) return ibm_fail(IBM_E_INVALID, "ibm_net_target: null argument");
+    if (!(s > 0.0) || !isfinite(s)) return ibm_fail(IBM_E_INVALID, "ibm_net_target: the scale must be positive");
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    k_net_target<<<blocks_n(N, 256), 256, 0, (cudaStream_t)stream>>>(N, d_pnext, d_p, d_pprev, s, d_target);
+    IBM_LAUNCHED("ibm_net: target");
+    IBM_CUDA(cudaGetLastError());
+    return IBM_OK;
+}
+
+// One training step on a snapshot: features from (b, p, p_prev, flags) against the target of
+// ibm_net_target, forward, mean squared error, backward, Adam (lr; betas 0.9, 0.999).  *loss (host,
+// synchronises) = the mean squared error before the update.  lr = 0 computes the gradients only.
 extern "C" int ibm_net_train_step(ibm_net* n, const ibm_grid* g, const double* d_b, const double* d_p,
                                   const double* d_pprev, const uint8_t* d_flags, const float* d_target, float lr,
                                   double* loss, void* stream) {

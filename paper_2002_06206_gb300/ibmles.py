@@ -109,6 +109,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "ibm_net_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_float, C.c_void_p, C.c_void_p]),
+    "ibm_net_target": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                 C.c_void_p]),
     "les_attach_guess": (C.c_int, [C.c_void_p, C.c_void_p]),
     "les_last_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ibm_surface_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -452,6 +454,15 @@ class Net:
                                      _ptr(pprev, torch.float64), _ptr(flags, torch.uint8) if flags is not None else None,
                                      _ptr(out, torch.float32), C.byref(s), _stream(stream)))
         return out, s.value
+
+    def target(self, grid, pnext, p, pprev, s, stream=None):
+        """(p^{n+1} - 2 p^n + p^{n-1}) / s in FP32, formed on the device (ibm_net_target)."""
+        N = grid.nx * grid.ny * grid.nz
+        out = torch.empty(N, dtype=torch.float32, device=p.device)
+        _check(lib().ibm_net_target(C.byref(grid), _ptr(pnext, torch.float64), _ptr(p, torch.float64),
+                                    _ptr(pprev, torch.float64), C.c_double(s), _ptr(out, torch.float32),
+                                    _stream(stream)))
+        return out
 
     def train_step(self, grid, b, p, pprev, target, lr, flags=None, stream=None):
         loss = C.c_double()
