@@ -98,6 +98,22 @@ def test_network_forward_and_gradients_match_reference(L, shape):
     net.close()
 
 
+def test_training_target_is_the_second_difference_over_the_scale(L):
+    nx, ny, nz = 48, 40, 36
+    g = L.make_grid(nx, ny, nz)
+    rng = np.random.default_rng(11)
+    pn1, p, pp = (rng.standard_normal(nx * ny * nz) for _ in range(3))
+    t = lambda a: torch.from_numpy(a).to("cuda", torch.float64)
+    net = L.Net(flat_params(*NL.init_params(seed=1, scale=0.05)))
+    out = net.target(g, t(pn1), t(p), t(pp), 0.37).cpu().numpy()
+    # FP64 in this order, then rounded to FP32: exactly
+    assert np.array_equal(out, ((pn1 - 2.0 * p + pp) / 0.37).astype(np.float32))
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(L.IbmError):
+            net.target(g, t(pn1), t(p), t(pp), bad)
+    net.close()
+
+
 def test_training_lowers_the_loss(L):
     shape = (16, 16, 32)
     nz, ny, nx = shape
@@ -146,7 +162,7 @@ def test_trained_guess_lowers_the_initial_residual(L):
     for epoch in range(6):
         for (b, p_n, p_p, p_next) in snaps:
             _, s = net.forward(g, b, p_n, p_p, geo.flags)
-            target = ((p_next - 2.0 * p_n + p_p) / s).to(torch.float32)
+            target = net.target(g, p_next, p_n, p_p, s)
             net.train_step(g, b, p_n, p_p, target, 2e-3, geo.flags)
 
     Ax = torch.empty(N, dtype=torch.float64, device="cuda")
